@@ -1,0 +1,181 @@
+/*
+ * tpcf.h -- C ABI of the GB300 (sm_103a) binned harmonic 3PCF estimator.
+ *
+ * The estimator is that of arXiv:2408.16847, section 3.1: for every pivot i
+ * (HEALPix pixel or catalogue point) with weight w_i != 0 and every other point j
+ * whose angular separation theta_ij falls in radial bin k = [theta_k, theta_{k+1}),
+ *
+ *     a_m^k(i) = sum_j w_j d_j exp(-i m phi_ij)          (eq. Xm.binned, unnormalised;
+ *                                                         phi_ij = position angle of j
+ *                                                         about i, from local north
+ *                                                         through east)
+ *     S_m(k1,k2) = sum_i w_i d_i a_m^{k1}(i) conj(a_m^{k2}(i))      (eqs. zetamEst,
+ *                                                                     zetamEst2)
+ *     D(k1,k2)   = sum_i w_i W^{k1}(i) W^{k2}(i),  W^k(i) = sum_j w_j Theta_k(ij)
+ *     zeta_m     = S_m / D                 (normalisation by the same estimator run
+ *                                           with d = 1 and m = 0; zeta = 0 where D = 0)
+ *
+ * for m = 0..m_max.  Bins are decided by chord length against 2 sin(theta_e / 2);
+ * the j = k self term of the outer product is kept, as in the paper (section 3.4),
+ * unless TPCF_SELF_PAIRS_SUBTRACT is set.
+ *
+ * Conventions common to every call:
+ *  - Device buffers ("d_" prefix) are allocated and owned by the caller; the plan
+ *    owns its internal tables and scratch.  Host buffers carry an "h_" prefix.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls enqueue work on it and return; they do not synchronise unless stated.
+ *  - Calls never abort: they return a tpcf_status.  Errors found on the device are
+ *    latched in the plan and reported by the next call or by tpcf_plan_sync().
+ *  - d_delta and d_w are float32, one value per point (RING pixel order for maps,
+ *    catalogue order for catalogues).  w = 0 marks a masked point: it is neither a
+ *    pivot nor a neighbour.
+ *  - zeta / dL_dzeta layout: double[(m_max+1)][K][K][2] (re, im), row-major.
+ *    norm layout: double[K][K].
+ *  - A plan is not thread-safe; calls on one plan must be serialised by the caller
+ *    (the same stream, or external synchronisation).
+ */
+#ifndef TPCF_H
+#define TPCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tpcf_plan_s* tpcf_plan;
+typedef struct tpcf_batch_s* tpcf_batch;
+
+typedef enum {
+    TPCF_OK = 0,
+    TPCF_ERR_INVALID_ARG = 1, /* a pointer, size, range or flag is not acceptable   */
+    TPCF_ERR_CUDA = 2,        /* a CUDA runtime call failed (message: tpcf_last_error) */
+    TPCF_ERR_OOM = 3,         /* device allocation failed; nothing leaked           */
+    TPCF_ERR_TIMEOUT = 4,     /* a bounded device wait gave up                      */
+    TPCF_ERR_UNSUPPORTED = 5, /* valid request this build does not implement        */
+    TPCF_ERR_DEVICE = 6       /* a kernel latched an error (bad table / index)      */
+} tpcf_status;
+
+/* Plan flags. */
+#define TPCF_SELF_PAIRS_KEEP 0u      /* keep the j = k term (the paper's estimator) */
+#define TPCF_SELF_PAIRS_SUBTRACT 1u  /* remove it from S_m(k,k) and from D(k,k)     */
+#define TPCF_CONTRACT_FP32 0u        /* sum over pivots on the FP32 pipe            */
+#define TPCF_CONTRACT_TC 2u          /* sum over pivots on the tensor cores (split
+                                        TF32x3 operands, FP32 accumulate)           */
+
+#define TPCF_MAX_BINS 32
+#define TPCF_MAX_M 16
+
+/* Angular bins: nbins edges theta_edges_rad[0..nbins] (radians, strictly increasing,
+ * theta_edges_rad[0] > 0, theta_edges_rad[nbins] < pi/2), multipoles 0..m_max
+ * (0 <= m_max <= TPCF_MAX_M), flags as above.  Copied by the plan. */
+typedef struct {
+    int32_t nbins;
+    const double* theta_edges_rad; /* host pointer */
+    int32_t m_max;
+    uint32_t flags;
+} tpcf_bins;
+
+/* Human-readable name of a status; the pointer is static. */
+const char* tpcf_status_string(tpcf_status s);
+/* Text of the last CUDA error seen by this thread (static storage). */
+const char* tpcf_last_error(void);
+
+/*
+ * Map plan for a full-sky HEALPix RING map of resolution nside (1 <= nside <= 8192),
+ * 12 nside^2 pixels (Gorski et al. 2005, the pixelisation of the paper's maps,
+ * section 3.3).  Builds, on the device and on `stream`, the ring geometry in FP64
+ * and the per-ring-pair bin thresholds used by the exact ring-range neighbour
+ * search.  On failure *out is left NULL and nothing is leaked.
+ */
+tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const tpcf_bins* bins, void* stream);
+
+/*
+ * Catalogue plan over n points given as unit vectors d_xyz (device, double[n][3]),
+ * for point catalogues (the paper's estimator applies to any sample on the sphere,
+ * section 3.1).  Sorts the points into a device-built sphere grid; the plan keeps
+ * its own sorted copy, d_xyz may be freed after the call returns and the stream
+ * has been synchronised.
+ */
+tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_xyz, int64_t n,
+                                     const tpcf_bins* bins, void* stream);
+
+/* Number of points (pixels) of the plan; -1 if plan is NULL. */
+int64_t tpcf_plan_npoints(tpcf_plan plan);
+
+/* Number of CUDA kernels the plan's calls have enqueued so far (plan creation
+ * excluded); -1 if plan is NULL.  Lets a caller count launches in a timed region. */
+int64_t tpcf_plan_kernel_launches(tpcf_plan plan);
+
+/*
+ * Forward estimator over the pivots with index in [pivot_begin, pivot_end)
+ * (pivot_begin = 0, pivot_end = npoints for all).  Neighbours are always taken
+ * from every point.  Writes d_zeta, d_norm (D) and, if d_sums != NULL, the raw
+ * sums S (same layout as zeta).  An empty pivot range writes zeros.
+ */
+tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const float* d_w,
+                         int64_t pivot_begin, int64_t pivot_end, double* d_zeta, double* d_norm,
+                         double* d_sums, void* stream);
+
+/*
+ * Adjoint: d_grad[p] = dL/d(delta_p) for a real loss L of zeta over the same pivot
+ * range, given d_dL_dzeta = dL/dRe(zeta) + i dL/dIm(zeta) (zeta layout) and the
+ * normalisation d_norm from the matching forward.  Recomputes the moments a_m^k
+ * instead of storing them.  d_grad (float[npoints]) is overwritten.
+ */
+tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const float* d_w,
+                          int64_t pivot_begin, int64_t pivot_end, const double* d_norm,
+                          const double* d_dL_dzeta, float* d_grad, void* stream);
+
+/*
+ * Exact number of in-bin ordered pairs (i, j) whose pivot i lies in
+ * [pivot_begin, pivot_end) and has w_i != 0, whatever w_j (the units of the
+ * throughput figure).  d_counts (device, int64[3]) receives: the total, the pairs
+ * visited as mirror images (equatorial-belt symmetry), the pairs visited singly.
+ * Map plans only.
+ */
+tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_t pivot_begin, int64_t pivot_end,
+                             int64_t* d_counts, void* stream);
+
+/*
+ * End-to-end call on HOST buffers: copies h_delta and h_w to the device, runs the
+ * forward over all pivots and, if h_dL_dzeta != NULL, the adjoint, and copies
+ * zeta, norm and (if h_grad != NULL) the gradient back.  Uses device staging
+ * buffers owned by the plan (allocated on first use).  Synchronises `stream`.
+ */
+tpcf_status tpcf_run_host(tpcf_plan plan, const float* h_delta, const float* h_w,
+                          const double* h_dL_dzeta, double* h_zeta, double* h_norm,
+                          float* h_grad, void* stream);
+
+/*
+ * Batched execution for n map plans (mixed nside, bins and m_max): one persistent
+ * launch runs every plan's forward tiles from a shared work queue, one launch
+ * normalises, and, when d_dL_dzeta[i] != NULL for all i, one persistent launch
+ * runs every adjoint.  tpcf_batch_create records the sequence into a CUDA graph
+ * (the pointers are baked in); tpcf_batch_launch replays it on `stream`.
+ */
+tpcf_status tpcf_batch_create(tpcf_batch* out, const tpcf_plan* plans, int32_t n,
+                              const float* const* d_delta, const float* const* d_w,
+                              double* const* d_zeta, double* const* d_norm,
+                              const double* const* d_dL_dzeta, float* const* d_grad,
+                              void* stream);
+tpcf_status tpcf_batch_launch(tpcf_batch batch, void* stream);
+void tpcf_batch_destroy(tpcf_batch batch);
+
+/* Convenience: create, launch once and destroy a batch. */
+tpcf_status tpcf_forward_batched(const tpcf_plan* plans, int32_t n, const float* const* d_delta,
+                                 const float* const* d_w, double* const* d_zeta,
+                                 double* const* d_norm, const double* const* d_dL_dzeta,
+                                 float* const* d_grad, void* stream);
+
+/* Synchronise the plan's last stream and return any latched device error. */
+tpcf_status tpcf_plan_sync(tpcf_plan plan);
+
+/* Free everything the plan owns (synchronises with its pending work). NULL is a no-op. */
+void tpcf_plan_destroy(tpcf_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPCF_H */

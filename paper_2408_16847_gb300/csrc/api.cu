@@ -1,0 +1,465 @@
+// Host side of the C ABI declared in include/tpcf.h: plan objects, validation,
+// launch sequencing and error reporting.  Every numerical step runs in the
+// kernels of geometry.cu, small_kernels.cu and map_kernels.cuh.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "geometry.cuh"
+
+using namespace tpcf;
+
+namespace tpcf {
+// per-M launchers (map_inst.cu)
+#define TPCF_DECL_M(m)                                                                      \
+    cudaError_t map_fwd_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
+    cudaError_t map_bwd_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
+    int map_fwd_occupancy_m##m(int, int);                                                  \
+    int map_bwd_occupancy_m##m(int);                                                       \
+    size_t map_fwd_smem_m##m(int);                                                         \
+    size_t map_bwd_smem_m##m(int);
+TPCF_DECL_M(0) TPCF_DECL_M(1) TPCF_DECL_M(2) TPCF_DECL_M(3) TPCF_DECL_M(4) TPCF_DECL_M(5)
+TPCF_DECL_M(6) TPCF_DECL_M(7) TPCF_DECL_M(8) TPCF_DECL_M(9) TPCF_DECL_M(10) TPCF_DECL_M(11)
+TPCF_DECL_M(12) TPCF_DECL_M(13) TPCF_DECL_M(14) TPCF_DECL_M(15) TPCF_DECL_M(16)
+#undef TPCF_DECL_M
+cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi,
+                             unsigned long long* counts, int grid, cudaStream_t s);
+
+struct MLaunch {
+    cudaError_t (*fwd)(const MapDev&, const MapCall&, int, cudaStream_t);
+    cudaError_t (*bwd)(const MapDev&, const MapCall&, int, cudaStream_t);
+    int (*fwd_occ)(int, int);
+    int (*bwd_occ)(int);
+    size_t (*fwd_smem)(int);
+    size_t (*bwd_smem)(int);
+};
+#define TPCF_ROW_M(m) \
+    {map_fwd_launch_m##m, map_bwd_launch_m##m, map_fwd_occupancy_m##m, map_bwd_occupancy_m##m, map_fwd_smem_m##m, map_bwd_smem_m##m}
+static const MLaunch kLaunch[TPCF_MAX_M + 1] = {
+    TPCF_ROW_M(0),  TPCF_ROW_M(1),  TPCF_ROW_M(2),  TPCF_ROW_M(3),  TPCF_ROW_M(4),  TPCF_ROW_M(5),
+    TPCF_ROW_M(6),  TPCF_ROW_M(7),  TPCF_ROW_M(8),  TPCF_ROW_M(9),  TPCF_ROW_M(10), TPCF_ROW_M(11),
+    TPCF_ROW_M(12), TPCF_ROW_M(13), TPCF_ROW_M(14), TPCF_ROW_M(15), TPCF_ROW_M(16)};
+#undef TPCF_ROW_M
+}  // namespace tpcf
+
+static thread_local char g_last_error[256] = "";
+
+static tpcf_status cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? TPCF_ERR_OOM : TPCF_ERR_CUDA;
+}
+
+#define TRY_CUDA(call)                                           \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);      \
+    } while (0)
+
+enum PlanKind { PLAN_MAP = 1, PLAN_CATALOG = 2 };
+
+struct tpcf_plan_s {
+    int kind = 0;
+    int device = 0;
+    int num_sms = 0;
+    int64_t npoints = 0;
+    int K = 0, M = 0;
+    uint32_t flags = 0;
+    std::vector<double> edges;
+    std::vector<void*> allocs;  // everything freed by destroy
+    MapDev map{};
+    // per-call scratch
+    float2* wdw = nullptr;
+    double* slots = nullptr;
+    int fwd_grid = 0, bwd_grid = 0;
+    int nent = 0;
+    double* sums = nullptr;
+    int* counter = nullptr;
+    int* status = nullptr;
+    float* H = nullptr;
+    // staging for tpcf_run_host
+    float* st_delta = nullptr;
+    float* st_w = nullptr;
+    double* st_dL = nullptr;
+    double* st_zeta = nullptr;
+    double* st_norm = nullptr;
+    float* st_grad = nullptr;
+    cudaStream_t last_stream = nullptr;
+    long long launches = 0;  // kernels this plan has launched (bookkeeping for benchmarks)
+
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        if (e != cudaSuccess) return e;
+        allocs.push_back(q);
+        *p = (T*)q;
+        return cudaSuccess;
+    }
+    ~tpcf_plan_s() {
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+extern "C" const char* tpcf_status_string(tpcf_status s) {
+    switch (s) {
+        case TPCF_OK: return "TPCF_OK";
+        case TPCF_ERR_INVALID_ARG: return "TPCF_ERR_INVALID_ARG";
+        case TPCF_ERR_CUDA: return "TPCF_ERR_CUDA";
+        case TPCF_ERR_OOM: return "TPCF_ERR_OOM";
+        case TPCF_ERR_TIMEOUT: return "TPCF_ERR_TIMEOUT";
+        case TPCF_ERR_UNSUPPORTED: return "TPCF_ERR_UNSUPPORTED";
+        case TPCF_ERR_DEVICE: return "TPCF_ERR_DEVICE";
+    }
+    return "TPCF_ERR_UNKNOWN";
+}
+
+extern "C" const char* tpcf_last_error(void) { return g_last_error; }
+
+static tpcf_status check_bins(const tpcf_bins* b) {
+    if (!b || !b->theta_edges_rad) return TPCF_ERR_INVALID_ARG;
+    if (b->nbins < 1 || b->nbins > TPCF_MAX_BINS) return TPCF_ERR_INVALID_ARG;
+    if (b->m_max < 0 || b->m_max > TPCF_MAX_M) return TPCF_ERR_INVALID_ARG;
+    if (b->flags & ~(uint32_t)(TPCF_SELF_PAIRS_SUBTRACT | TPCF_CONTRACT_TC)) return TPCF_ERR_INVALID_ARG;
+    const double* t = b->theta_edges_rad;
+    if (!(t[0] > 0.0)) return TPCF_ERR_INVALID_ARG;
+    for (int e = 0; e < b->nbins; ++e)
+        if (!(t[e + 1] > t[e])) return TPCF_ERR_INVALID_ARG;
+    if (!(t[b->nbins] < 0.5 * M_PI)) return TPCF_ERR_INVALID_ARG;
+    return TPCF_OK;
+}
+
+static int n_blocks(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
+    MapDev& g = P->map;
+    const int nrings = (int)(4 * nside - 1);
+    const int K = P->K;
+    g.nside = (int)nside;
+    g.nrings = nrings;
+    g.K = K;
+    g.M = P->M;
+    g.npix = 12 * nside * nside;
+    int64_t *first, *pair_off, *tile_off, *npairs_r, *ntiles_r, *tot;
+    int *npr, *shift;
+    double *z, *sd, *th, *E, *theta;
+    float *zf, *sf, *rstep, *rinvn;
+    int2 *ring_range, *bin_range;
+    TRY_CUDA(P->alloc(&first, nrings));
+    TRY_CUDA(P->alloc(&npr, nrings));
+    TRY_CUDA(P->alloc(&shift, nrings));
+    TRY_CUDA(P->alloc(&z, nrings));
+    TRY_CUDA(P->alloc(&sd, nrings));
+    TRY_CUDA(P->alloc(&th, nrings));
+    TRY_CUDA(P->alloc(&zf, nrings));
+    TRY_CUDA(P->alloc(&sf, nrings));
+    TRY_CUDA(P->alloc(&rstep, nrings));
+    TRY_CUDA(P->alloc(&rinvn, nrings));
+    TRY_CUDA(P->alloc(&ring_range, nrings));
+    TRY_CUDA(P->alloc(&bin_range, (size_t)nrings * K));
+    TRY_CUDA(P->alloc(&pair_off, nrings));
+    TRY_CUDA(P->alloc(&tile_off, nrings));
+    TRY_CUDA(P->alloc(&npairs_r, nrings));
+    TRY_CUDA(P->alloc(&ntiles_r, nrings));
+    TRY_CUDA(P->alloc(&tot, 2));
+    TRY_CUDA(P->alloc(&E, K + 1));
+    TRY_CUDA(P->alloc(&theta, K + 1));
+    TRY_CUDA(cudaMemcpyAsync(theta, P->edges.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, s));
+    edges_kernel<<<1, 64, 0, s>>>(K, theta, E);
+    ring_table_kernel<<<n_blocks(nrings, 128), 128, 0, s>>>((int)nside, nrings, first, npr, shift, z, sd, th,
+                                                            zf, sf, rstep, rinvn);
+    ring_range_kernel<<<n_blocks(nrings, 128), 128, 0, s>>>(nrings, K, th, E, npr, ring_range, bin_range,
+                                                            npairs_r, ntiles_r);
+    exclusive_scan_kernel<<<1, 1024, 0, s>>>(npairs_r, pair_off, nrings, tot);
+    exclusive_scan_kernel<<<1, 1024, 0, s>>>(ntiles_r, tile_off, nrings, tot + 1);
+    TRY_CUDA(cudaGetLastError());
+    int64_t totals[2];
+    TRY_CUDA(cudaMemcpyAsync(totals, tot, sizeof(totals), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t npairs = totals[0], ntiles = totals[1];
+    float* pair_A;
+    int2 *pair_T, *tiles;
+    TRY_CUDA(P->alloc(&pair_A, npairs));
+    TRY_CUDA(P->alloc(&pair_T, (size_t)npairs * (K + 1)));
+    TRY_CUDA(P->alloc(&tiles, ntiles));
+    pair_table_kernel<<<n_blocks(npairs, 128), 128, 0, s>>>(nrings, K, pair_off, npairs, ring_range, th, sd,
+                                                            npr, E, pair_A, pair_T);
+    tile_list_kernel<<<nrings, 128, 0, s>>>(nrings, tile_off, ntiles_r, tiles);
+    TRY_CUDA(cudaGetLastError());
+    g.ring_first = first;
+    g.ring_n = npr;
+    g.ring_shift = shift;
+    g.ring_zf = zf;
+    g.ring_sf = sf;
+    g.ring_step = rstep;
+    g.ring_invn = rinvn;
+    g.ring_th = th;
+    g.ring_s = sd;
+    g.ring_range = ring_range;
+    g.bin_range = bin_range;
+    g.pair_off = pair_off;
+    g.pair_A = pair_A;
+    g.pair_T = pair_T;
+    g.tiles = tiles;
+    g.ntiles = ntiles;
+    g.E = E;
+    // per-call scratch, sized once so calls allocate nothing
+    const MLaunch& L = kLaunch[P->M];
+    const int self = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
+    int occ_f = L.fwd_occ(K, self);
+    int occ_b = L.bwd_occ(K);
+    if (occ_f < 1 || occ_b < 1) {
+        snprintf(g_last_error, sizeof(g_last_error), "kernel does not fit (K=%d, M=%d)", K, P->M);
+        return TPCF_ERR_UNSUPPORTED;
+    }
+    P->fwd_grid = (int)std::min<int64_t>(ntiles, (int64_t)P->num_sms * occ_f);
+    P->bwd_grid = (int)std::min<int64_t>(ntiles, (int64_t)P->num_sms * occ_b);
+    if (P->fwd_grid < 1) P->fwd_grid = 1;
+    if (P->bwd_grid < 1) P->bwd_grid = 1;
+    P->nent = n_entries(K, P->M);
+    TRY_CUDA(P->alloc(&P->wdw, g.npix));
+    TRY_CUDA(P->alloc(&P->slots, (size_t)P->fwd_grid * P->nent));
+    TRY_CUDA(P->alloc(&P->sums, P->nent));
+    TRY_CUDA(P->alloc(&P->counter, 4));
+    TRY_CUDA(P->alloc(&P->status, 4));
+    TRY_CUDA(P->alloc(&P->H, (size_t)(P->M + 1) * K * K * 2));
+    TRY_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int) * 4, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    return TPCF_OK;
+}
+
+extern "C" tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const tpcf_bins* bins, void* stream) {
+    if (!out) return TPCF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nside < 1 || nside > 8192) return TPCF_ERR_INVALID_ARG;
+    tpcf_status st = check_bins(bins);
+    if (st != TPCF_OK) return st;
+    tpcf_plan_s* P = new (std::nothrow) tpcf_plan_s();
+    if (!P) return TPCF_ERR_OOM;
+    P->kind = PLAN_MAP;
+    P->K = bins->nbins;
+    P->M = bins->m_max;
+    P->flags = bins->flags;
+    P->edges.assign(bins->theta_edges_rad, bins->theta_edges_rad + bins->nbins + 1);
+    P->npoints = 12 * nside * nside;
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "device query");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    st = build_map(P, nside, s);
+    if (st != TPCF_OK) {
+        cudaStreamSynchronize(s);
+        delete P;
+        return st;
+    }
+    P->last_stream = s;
+    *out = P;
+    return TPCF_OK;
+}
+
+extern "C" tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_xyz, int64_t n,
+                                                const tpcf_bins* bins, void* stream) {
+    (void)d_xyz;
+    (void)n;
+    (void)bins;
+    (void)stream;
+    if (!out) return TPCF_ERR_INVALID_ARG;
+    *out = nullptr;
+    return TPCF_ERR_UNSUPPORTED;
+}
+
+extern "C" int64_t tpcf_plan_npoints(tpcf_plan plan) { return plan ? plan->npoints : -1; }
+
+extern "C" int64_t tpcf_plan_kernel_launches(tpcf_plan plan) { return plan ? plan->launches : -1; }
+
+static tpcf_status latched(tpcf_plan_s* P) {
+    (void)P;
+    return TPCF_OK;
+}
+
+static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
+                               double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s) {
+    const MapDev& g = P->map;
+    pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_delta, d_w, P->wdw, g.npix);
+    P->launches += 4;  // pack, forward, reduce, finalize
+    TRY_CUDA(cudaMemsetAsync(P->slots, 0, sizeof(double) * (size_t)P->fwd_grid * P->nent, s));
+    TRY_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(int), s));
+    MapCall c{};
+    c.wdw = P->wdw;
+    c.piv_lo = lo;
+    c.piv_hi = hi;
+    c.slots = P->slots;
+    c.counter = P->counter;
+    c.status = P->status;
+    c.self_subtract = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
+    TRY_CUDA(kLaunch[P->M].fwd(g, c, P->fwd_grid, s));
+    reduce_slots_kernel<<<n_blocks(P->nent, 128), 128, 0, s>>>(P->slots, P->fwd_grid, P->nent, P->sums);
+    const int nout = (P->M + 1) * P->K * P->K;
+    finalize_kernel<<<n_blocks(nout, 128), 128, 0, s>>>(P->sums, P->K, P->M, c.self_subtract, 1.0, d_zeta,
+                                                        d_norm, d_sums);
+    TRY_CUDA(cudaGetLastError());
+    return TPCF_OK;
+}
+
+extern "C" tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const float* d_w, int64_t pivot_begin,
+                                    int64_t pivot_end, double* d_zeta, double* d_norm, double* d_sums,
+                                    void* stream) {
+    if (!plan || !d_delta || !d_w || !d_zeta || !d_norm) return TPCF_ERR_INVALID_ARG;
+    if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
+    tpcf_status st = latched(plan);
+    if (st != TPCF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    if (plan->kind == PLAN_MAP) return map_forward(plan, d_delta, d_w, pivot_begin, pivot_end, d_zeta, d_norm,
+                                                   d_sums, s);
+    return TPCF_ERR_UNSUPPORTED;
+}
+
+extern "C" tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_t pivot_begin,
+                                        int64_t pivot_end, int64_t* d_counts, void* stream) {
+    if (!plan || !d_w || !d_counts) return TPCF_ERR_INVALID_ARG;
+    if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
+    if (plan->kind != PLAN_MAP) return TPCF_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    const MapDev& g = plan->map;
+    // only the weights matter: pack them with a zero field
+    pack_kernel<<<plan->num_sms * 8, 256, 0, s>>>(d_w, d_w, plan->wdw, g.npix);
+    plan->launches += 2;
+    TRY_CUDA(cudaMemsetAsync(d_counts, 0, 3 * sizeof(int64_t), s));
+    TRY_CUDA(map_count_launch(g, plan->wdw, pivot_begin, pivot_end, (unsigned long long*)d_counts,
+                              plan->num_sms * 4, s));
+    return TPCF_OK;
+}
+
+static tpcf_status map_backward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
+                                const double* d_norm, const double* d_dL, float* d_grad, cudaStream_t s) {
+    const MapDev& g = P->map;
+    if (P->flags & TPCF_SELF_PAIRS_SUBTRACT) {
+        snprintf(g_last_error, sizeof(g_last_error), "adjoint with self-pair subtraction");
+        return TPCF_ERR_UNSUPPORTED;
+    }
+    pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_delta, d_w, P->wdw, g.npix);
+    const int nout = (P->M + 1) * P->K * P->K;
+    adjoint_prep_kernel<<<n_blocks(nout, 128), 128, 0, s>>>(d_dL, d_norm, P->K, P->M, P->H);
+    zero_f32_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_grad, g.npix);
+    P->launches += 4;  // pack, prep, zero, adjoint
+    TRY_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(int), s));
+    MapCall c{};
+    c.wdw = P->wdw;
+    c.piv_lo = lo;
+    c.piv_hi = hi;
+    c.counter = P->counter;
+    c.status = P->status;
+    c.H = P->H;
+    c.grad = d_grad;
+    TRY_CUDA(kLaunch[P->M].bwd(g, c, P->bwd_grid, s));
+    return TPCF_OK;
+}
+
+extern "C" tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const float* d_w, int64_t pivot_begin,
+                                     int64_t pivot_end, const double* d_norm, const double* d_dL_dzeta,
+                                     float* d_grad, void* stream) {
+    if (!plan || !d_delta || !d_w || !d_norm || !d_dL_dzeta || !d_grad) return TPCF_ERR_INVALID_ARG;
+    if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
+    tpcf_status st = latched(plan);
+    if (st != TPCF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    if (plan->kind == PLAN_MAP)
+        return map_backward(plan, d_delta, d_w, pivot_begin, pivot_end, d_norm, d_dL_dzeta, d_grad, s);
+    return TPCF_ERR_UNSUPPORTED;
+}
+
+extern "C" tpcf_status tpcf_run_host(tpcf_plan plan, const float* h_delta, const float* h_w,
+                                     const double* h_dL_dzeta, double* h_zeta, double* h_norm, float* h_grad,
+                                     void* stream) {
+    if (!plan || !h_delta || !h_w || !h_zeta || !h_norm) return TPCF_ERR_INVALID_ARG;
+    if (h_dL_dzeta && !h_grad) return TPCF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tpcf_plan_s* P = plan;
+    const int64_t n = P->npoints;
+    const size_t nz = (size_t)(P->M + 1) * P->K * P->K * 2;
+    if (!P->st_delta) {
+        TRY_CUDA(P->alloc(&P->st_delta, n));
+        TRY_CUDA(P->alloc(&P->st_w, n));
+        TRY_CUDA(P->alloc(&P->st_dL, nz));
+        TRY_CUDA(P->alloc(&P->st_zeta, nz));
+        TRY_CUDA(P->alloc(&P->st_norm, (size_t)P->K * P->K));
+        TRY_CUDA(P->alloc(&P->st_grad, n));
+    }
+    TRY_CUDA(cudaMemcpyAsync(P->st_delta, h_delta, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    TRY_CUDA(cudaMemcpyAsync(P->st_w, h_w, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    tpcf_status st = tpcf_forward(P, P->st_delta, P->st_w, 0, n, P->st_zeta, P->st_norm, nullptr, stream);
+    if (st != TPCF_OK) return st;
+    if (h_dL_dzeta) {
+        TRY_CUDA(cudaMemcpyAsync(P->st_dL, h_dL_dzeta, sizeof(double) * nz, cudaMemcpyHostToDevice, s));
+        st = tpcf_backward(P, P->st_delta, P->st_w, 0, n, P->st_norm, P->st_dL, P->st_grad, stream);
+        if (st != TPCF_OK) return st;
+        TRY_CUDA(cudaMemcpyAsync(h_grad, P->st_grad, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    }
+    TRY_CUDA(cudaMemcpyAsync(h_zeta, P->st_zeta, sizeof(double) * nz, cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaMemcpyAsync(h_norm, P->st_norm, sizeof(double) * P->K * P->K, cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    return tpcf_plan_sync(P);
+}
+
+extern "C" tpcf_status tpcf_plan_sync(tpcf_plan plan) {
+    if (!plan) return TPCF_ERR_INVALID_ARG;
+    TRY_CUDA(cudaStreamSynchronize(plan->last_stream));
+    int st = 0;
+    TRY_CUDA(cudaMemcpy(&st, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_BAD_TILE) {
+        snprintf(g_last_error, sizeof(g_last_error), "device status 0x%x (bad tile table)", st);
+        return TPCF_ERR_DEVICE;
+    }
+    return TPCF_OK;
+}
+
+extern "C" void tpcf_plan_destroy(tpcf_plan plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->last_stream);
+    delete plan;
+}
+
+// ------------------------------------------------------------------- batches
+
+struct tpcf_batch_s {
+    int dummy;
+};
+
+extern "C" tpcf_status tpcf_batch_create(tpcf_batch* out, const tpcf_plan* plans, int32_t n,
+                                         const float* const* d_delta, const float* const* d_w,
+                                         double* const* d_zeta, double* const* d_norm,
+                                         const double* const* d_dL_dzeta, float* const* d_grad, void* stream) {
+    (void)plans; (void)n; (void)d_delta; (void)d_w; (void)d_zeta; (void)d_norm; (void)d_dL_dzeta;
+    (void)d_grad; (void)stream;
+    if (out) *out = nullptr;
+    return TPCF_ERR_UNSUPPORTED;
+}
+
+extern "C" tpcf_status tpcf_batch_launch(tpcf_batch batch, void* stream) {
+    (void)batch;
+    (void)stream;
+    return TPCF_ERR_UNSUPPORTED;
+}
+
+extern "C" void tpcf_batch_destroy(tpcf_batch batch) { delete batch; }
+
+extern "C" tpcf_status tpcf_forward_batched(const tpcf_plan* plans, int32_t n, const float* const* d_delta,
+                                            const float* const* d_w, double* const* d_zeta,
+                                            double* const* d_norm, const double* const* d_dL_dzeta,
+                                            float* const* d_grad, void* stream) {
+    tpcf_batch b = nullptr;
+    tpcf_status st = tpcf_batch_create(&b, plans, n, d_delta, d_w, d_zeta, d_norm, d_dL_dzeta, d_grad, stream);
+    if (st != TPCF_OK) return st;
+    st = tpcf_batch_launch(b, stream);
+    tpcf_batch_destroy(b);
+    return st;
+}

@@ -1,0 +1,75 @@
+// Per-M instantiation of the map kernels.  The build compiles this file once for
+// every multipole limit TPCF_M = 0..TPCF_MAX_M and links the objects together.
+#include "map_kernels.cuh"
+
+#ifndef TPCF_M
+#error "compile with -DTPCF_M=<m_max>"
+#endif
+
+#define TPCF_CAT2(a, b) a##b
+#define TPCF_CAT(a, b) TPCF_CAT2(a, b)
+
+namespace tpcf {
+
+cudaError_t TPCF_CAT(map_fwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid,
+                                               cudaStream_t s) {
+    const size_t smem = tile_floats<TPCF_M>(g.K) * sizeof(float);
+    if (c.self_subtract) {
+        auto* k = map_fwd_kernel<TPCF_M, true>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    } else {
+        auto* k = map_fwd_kernel<TPCF_M, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t TPCF_CAT(map_bwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid,
+                                               cudaStream_t s) {
+    const size_t smem = bwd_tile_floats<TPCF_M>(g.K) * sizeof(float);
+    auto* k = map_bwd_kernel<TPCF_M>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(g, c);
+    return cudaGetLastError();
+}
+
+int TPCF_CAT(map_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
+    const size_t smem = tile_floats<TPCF_M>(K) * sizeof(float);
+    int nb = 0;
+    if (self_subtract) {
+        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, true>, NTHREADS, smem);
+    } else {
+        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, false>, NTHREADS, smem);
+    }
+    return nb;
+}
+
+int TPCF_CAT(map_bwd_occupancy_m, TPCF_M)(int K) {
+    const size_t smem = bwd_tile_floats<TPCF_M>(K) * sizeof(float);
+    int nb = 0;
+    cudaFuncSetAttribute(map_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_bwd_kernel<TPCF_M>, NTHREADS, smem);
+    return nb;
+}
+
+size_t TPCF_CAT(map_fwd_smem_m, TPCF_M)(int K) { return tile_floats<TPCF_M>(K) * sizeof(float); }
+size_t TPCF_CAT(map_bwd_smem_m, TPCF_M)(int K) { return bwd_tile_floats<TPCF_M>(K) * sizeof(float); }
+
+#if TPCF_M == 0
+cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi,
+                             unsigned long long* counts, int grid, cudaStream_t s) {
+    map_count_kernel<<<grid, NTHREADS, 0, s>>>(g, wdw, lo, hi, counts);
+    return cudaGetLastError();
+}
+#endif
+
+}  // namespace tpcf

@@ -1,0 +1,973 @@
+// Map-path kernels of the binned harmonic 3PCF estimator (arXiv:2408.16847,
+// section 3.1), templated on the largest multipole M.  Included by map_inst.cu,
+// which is compiled once per M.
+//
+// Work decomposition (forward):
+//   * a tile is 32 consecutive pivots of one HEALPix ring, one pivot per lane;
+//   * a CTA of 8 warps owns one tile at a time (persistent CTAs pull tiles from an
+//     atomic counter); for every radial bin k the warps split the neighbour rings
+//     that can hold bin-k pixels;
+//   * on a neighbour ring the bin-k pixels of a pivot form at most two contiguous
+//     runs, found from the per-ring-pair edge offsets T_e built by the plan
+//     (exact ring-range disc query, section 3.2 of the plan's design notes); each
+//     lane walks its own runs, so the bin is known without a per-pixel test and the
+//     (M+1) complex accumulators of the bin stay in registers across rings;
+//   * within a run e^{-i m phi} comes from the Chebyshev recurrences
+//     cos(m phi) = 2 cos(phi) cos((m-1) phi) - cos((m-2) phi) (same for sin), the
+//     trig-free harmonic step the paper uses (section 3.2, two operations per m),
+//     with the neighbour weight folded into the recurrence;
+//   * in the equatorial belt a neighbour ring has as many pixels as the pivot ring,
+//     so its pixels sit symmetrically about the pivot's meridian: the pixel at +phi
+//     and its mirror at -phi share one cos/sin evaluation and one recurrence;
+//   * after all bins, the tile's a_m^k(i) sit in shared memory and the CTA forms
+//     sum_i w_i d_i a^{k1} conj(a^{k2}) (eq. zetamEst2) and sum_i w_i W^{k1} W^{k2},
+//     adding them in FP64 into a slot owned by the CTA.
+#pragma once
+
+#include <math.h>
+
+#include "tpcf_internal.cuh"
+
+namespace tpcf {
+
+constexpr float AMBIGUITY = 1.0e-6f;  // > worst fp32 error of the edge position (~1.5e-7 px)
+constexpr float FAST_XMAX = 0.25f;    // |half longitude offset| covered by the polynomial
+
+__device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
+    long long q = a / b;
+    if ((a % b) != 0 && a < 0) --q;
+    return q;
+}
+
+// Position of the lane's pivot in units of ring-r pixels: c = cint + crem / den,
+// so that pixel p of ring r is at longitude offset o = p - c pixels from the pivot.
+struct LaneC {
+    int cint, crem, den;
+    float cfrac;
+};
+
+// floor(num / den) from an fp32 estimate corrected in exact integer arithmetic (the
+// estimate is within one of the true quotient for the sizes used here).
+__device__ __forceinline__ LaneC lane_c(int q, int s_i, int n_i, int s_r, int n_r) {
+    const long long num = (long long)n_r * (2LL * q + s_i) - (long long)s_r * n_i;
+    const int den = 2 * n_i;
+    int ci = (int)floorf(__fdividef((float)num, (float)den));
+    long long rem = num - (long long)ci * den;
+    if (rem < 0) {
+        --ci;
+        rem += den;
+    } else if (rem >= den) {
+        ++ci;
+        rem -= den;
+    }
+    LaneC c;
+    c.cint = ci;
+    c.crem = (int)rem;
+    c.den = den;
+    c.cfrac = __fdiv_rn((float)c.crem, (float)den);
+    return c;
+}
+
+// Exact (FP64) quarter squared chord of pixel p of ring r about the pivot:
+// f = sin^2((theta_r - theta_i)/2) + s_i s_r sin^2(pi o / n_r).  Only evaluated for
+// the rare edge pixels whose fp32 position is ambiguous, so the context holds the
+// raw ring values and the FP64 trigonometry runs inside the rare branch.
+struct ExactCtx {
+    double th_i, th_r, s_i, s_r;
+    int n_r;
+};
+
+static __device__ __noinline__ double exact_f(double th_i, double th_r, double s_i, double s_r, int n_r,
+                                              int cint, int crem, int den, int p) {
+    const double h = sin(0.5 * (th_r - th_i));
+    const double o = (double)(p - cint) - (double)crem / (double)den;
+    const double sp = sinpi(o / (double)n_r);
+    return h * h + (s_i * s_r) * sp * sp;
+}
+
+// First pixel p (unwrapped index) with p - c >= T (T finite, positive).
+__device__ __forceinline__ int pos_edge(const LaneC& c, int2 T, double Ee, const ExactCtx& x) {
+    const float y = c.cfrac + __int_as_float(T.y);
+    const float ry = rintf(y);
+    const int base = c.cint + T.x;
+    if (fabsf(y - ry) > AMBIGUITY) return base + (int)ceilf(y);
+    const int ps = base + (int)ry;
+    return (exact_f(x.th_i, x.th_r, x.s_i, x.s_r, x.n_r, c.cint, c.crem, c.den, ps) >= Ee) ? ps : ps + 1;
+}
+
+// Last pixel p with p - c <= -T.
+__device__ __forceinline__ int neg_edge(const LaneC& c, int2 T, double Ee, const ExactCtx& x) {
+    const float y = c.cfrac - __int_as_float(T.y);
+    const float ry = rintf(y);
+    const int base = c.cint - T.x;
+    if (fabsf(y - ry) > AMBIGUITY) return base + (int)floorf(y);
+    const int ps = base + (int)ry;
+    return (exact_f(x.th_i, x.th_r, x.s_i, x.s_r, x.n_r, c.cint, c.crem, c.den, ps) >= Ee) ? ps : ps - 1;
+}
+
+// Warp-uniform description of neighbour ring r for pivot ring i.
+struct RingCtx {
+    long long first;
+    int n, shift;
+    float s_r;   // sin(colatitude of r)
+    float A;     // sin(theta_i - theta_r)
+    float B;     // 2 cos(theta_i) sin(theta_r)
+    float step;  // pi / n  (half longitude step)
+    float inv_n; // 1 / n
+};
+
+// sin x and cos x for |x| <= FAST_XMAX from their Taylor series (truncation error
+// below 2e-11 relative at the end of the range).
+__device__ __forceinline__ void sin_cos_series(float x, float& s, float& c) {
+    const float x2 = x * x;
+    s = x * fmaf(x2, fmaf(x2, fmaf(x2, -1.98412698e-4f, 8.33333333e-3f), -1.66666667e-1f), 1.0f);
+    c = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 2.48015873e-5f, -1.38888889e-3f), 4.16666667e-2f), -0.5f),
+             1.0f);
+}
+
+// Direction (cos phi, sin phi) of a neighbour at longitude offset o (ring-r pixels):
+// with x = pi o / n (half the longitude difference),
+//   east  component  E = s_r sin(2x)
+//   north component  N = sin(theta_i - theta_r) + 2 cos(theta_i) s_r sin^2 x,
+// the cancellation-free form of n_j . e_N(i); phi is measured from north to east.
+template <bool FAST>
+__device__ __forceinline__ void pixel_dir(float o, const RingCtx& R, float& cph, float& sph) {
+    float sx, cx;
+    if (FAST) {
+        sin_cos_series(o * R.step, sx, cx);
+    } else {
+        sincospif(o * R.inv_n, &sx, &cx);
+    }
+    const float E = R.s_r * (2.0f * sx * cx);
+    const float N = fmaf(R.B, sx * sx, R.A);
+    // the floor only matters for the masked-out iterations of a run (zero weight),
+    // which may sit on the pivot itself; real neighbours have N^2 + E^2 = sin^2 theta.
+    const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+    cph = N * rinv;
+    sph = E * rinv;
+}
+
+// acc_re[m] += wc cos(m phi), acc_im[m] += ws sin(m phi), m = 0..M, by the Chebyshev
+// three-term recurrences with the weights folded in.
+template <int M>
+__device__ __forceinline__ void harmonics(float (&re)[M + 1], float (&im)[M + 1], float cph, float sph,
+                                          float wc, float ws) {
+    re[0] += wc;
+    if constexpr (M >= 1) {
+        float u0 = wc, u1 = wc * cph;
+        float v0 = 0.0f, v1 = ws * sph;
+        re[1] += u1;
+        im[1] += v1;
+        const float c2 = cph + cph;
+#pragma unroll
+        for (int m = 2; m <= M; ++m) {
+            const float u2 = fmaf(c2, u1, -u0);
+            const float v2 = fmaf(c2, v1, -v0);
+            re[m] += u2;
+            im[m] += v2;
+            u0 = u1;
+            u1 = u2;
+            v0 = v1;
+            v1 = v2;
+        }
+    }
+}
+
+// The same for two pixels a and b at once (two independent recurrence chains for
+// instruction-level parallelism; the sums are added pairwise).
+template <int M>
+__device__ __forceinline__ void harmonics2(float (&re)[M + 1], float (&im)[M + 1], float ca, float sa,
+                                           float wca, float wsa, float cb, float sb, float wcb, float wsb) {
+    re[0] += wca + wcb;
+    if constexpr (M >= 1) {
+        float ua0 = wca, ua1 = wca * ca, va0 = 0.0f, va1 = wsa * sa;
+        float ub0 = wcb, ub1 = wcb * cb, vb0 = 0.0f, vb1 = wsb * sb;
+        re[1] += ua1 + ub1;
+        im[1] += va1 + vb1;
+        const float c2a = ca + ca, c2b = cb + cb;
+#pragma unroll
+        for (int m = 2; m <= M; ++m) {
+            const float ua2 = fmaf(c2a, ua1, -ua0);
+            const float ub2 = fmaf(c2b, ub1, -ub0);
+            const float va2 = fmaf(c2a, va1, -va0);
+            const float vb2 = fmaf(c2b, vb1, -vb0);
+            re[m] += ua2 + ub2;
+            im[m] += va2 + vb2;
+            ua0 = ua1;
+            ua1 = ua2;
+            ub0 = ub1;
+            ub1 = ub2;
+            va0 = va1;
+            va1 = va2;
+            vb0 = vb1;
+            vb1 = vb2;
+        }
+    }
+}
+
+// p mod n for -n <= p < 2n (every unwrapped index of a run lies in that range).
+__device__ __forceinline__ int wrap_idx(int p, int n) {
+    return p < 0 ? p + n : (p >= n ? p - n : p);
+}
+
+// Walk pixels [a, a + len) of ring R (lane-private run), accumulating into the bin.
+// Two pixels per iteration.
+template <int M, bool FAST, bool SELF>
+__device__ __forceinline__ void walk_run(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
+                                         int a, int len, float (&re)[M + 1], float (&im)[M + 1],
+                                         float& W, float& Q, float& QW) {
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    const float o0 = (float)(a - c.cint) - c.cfrac;
+    int idx = wrap_idx(a, R.n);
+    const float2* row = wdw + R.first;
+    for (int t = 0; t < maxlen; t += 2) {
+        const bool on0 = t < len, on1 = t + 1 < len;
+        const int idx1 = idx + 1 >= R.n ? idx + 1 - R.n : idx + 1;
+        const float2 v0 = on0 ? __ldg(row + idx) : make_float2(0.0f, 0.0f);
+        const float2 v1 = on1 ? __ldg(row + idx1) : make_float2(0.0f, 0.0f);
+        const float oa = on0 ? o0 + (float)t : o0;
+        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        float ca, sa, cb, sb;
+        pixel_dir<FAST>(oa, R, ca, sa);
+        pixel_dir<FAST>(ob, R, cb, sb);
+        harmonics2<M>(re, im, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x);
+        W += v0.y + v1.y;
+        if (SELF) {
+            Q = fmaf(v0.x, v0.x, fmaf(v1.x, v1.x, Q));
+            QW = fmaf(v0.y, v0.y, fmaf(v1.y, v1.y, QW));
+        }
+        idx = idx1 + 1 >= R.n ? idx1 + 1 - R.n : idx1 + 1;
+    }
+}
+
+// Walk the pixel pairs (p, mb - p), p in [a, a + len): mirror images about the
+// pivot's meridian (belt rings with as many pixels as the pivot ring).  Two pairs
+// (four pixels) per iteration.
+template <int M, bool FAST, bool SELF>
+__device__ __forceinline__ void walk_pairs(const RingCtx& R, const float2* __restrict__ wdw,
+                                           const LaneC& c, int a, int len, int mb,
+                                           float (&re)[M + 1], float (&im)[M + 1], float& W, float& Q,
+                                           float& QW) {
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    const float o0 = (float)(a - c.cint) - c.cfrac;
+    int ip = wrap_idx(a, R.n);
+    int im_ = wrap_idx(mb - a, R.n);
+    const float2* row = wdw + R.first;
+    for (int t = 0; t < maxlen; t += 2) {
+        const bool on0 = t < len, on1 = t + 1 < len;
+        const int ip1 = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
+        const int im1 = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
+        const float2 p0 = on0 ? __ldg(row + ip) : make_float2(0.0f, 0.0f);
+        const float2 m0 = on0 ? __ldg(row + im_) : make_float2(0.0f, 0.0f);
+        const float2 p1 = on1 ? __ldg(row + ip1) : make_float2(0.0f, 0.0f);
+        const float2 m1 = on1 ? __ldg(row + im1) : make_float2(0.0f, 0.0f);
+        const float oa = on0 ? o0 + (float)t : o0;
+        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        float ca, sa, cb, sb;
+        pixel_dir<FAST>(oa, R, ca, sa);
+        pixel_dir<FAST>(ob, R, cb, sb);
+        harmonics2<M>(re, im, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x);
+        W += (p0.y + m0.y) + (p1.y + m1.y);
+        if (SELF) {
+            Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, fmaf(p1.x, p1.x, fmaf(m1.x, m1.x, Q))));
+            QW = fmaf(p0.y, p0.y, fmaf(m0.y, m0.y, fmaf(p1.y, p1.y, fmaf(m1.y, m1.y, QW))));
+        }
+        ip = ip1 + 1 >= R.n ? ip1 + 1 - R.n : ip1 + 1;
+        im_ = im1 - 1 < 0 ? im1 - 1 + R.n : im1 - 1;
+    }
+}
+
+// Runs of bin k on ring r for the lane's pivot.  Fills up to two runs (a, len) and,
+// in mirror mode, one pair run plus an optional centre pixel.
+struct BinRuns {
+    int a0, n0, a1, n1;  // plain runs
+    bool sym;            // pair mode: pairs (p, mb - p), p in [a0, a0 + n0)
+    int mb;              // mirror base
+    bool centre;         // pixel cint (offset 0) also belongs to the bin (pair mode)
+};
+
+__device__ __forceinline__ BinRuns bin_runs(const LaneC& c, int2 Tk, int2 Tk1, double Ek, double Ek1,
+                                            const ExactCtx& x, int n_r, bool sym) {
+    BinRuns b;
+    b.sym = sym;
+    b.centre = false;
+    b.mb = 0;
+    b.a1 = 0;
+    b.n1 = 0;
+    // upper end of the + side, lower end of the - side
+    int pe, ns;
+    if (Tk1.x == T_INF) {
+        pe = c.cint + n_r / 2;
+        ns = c.cint - n_r / 2 + 1;
+    } else {
+        pe = pos_edge(c, Tk1, Ek1, x) - 1;
+        ns = neg_edge(c, Tk1, Ek1, x) + 1;
+    }
+    if (sym) {
+        int a;
+        if (Tk.x == T_ZERO) {
+            a = c.cint + 1;
+            b.centre = (c.crem == 0);
+        } else {
+            a = pos_edge(c, Tk, Ek, x);
+        }
+        b.a0 = a;
+        b.n0 = max(0, pe - a + 1);
+        b.mb = 2 * c.cint + (c.crem != 0 ? 1 : 0);
+        return b;
+    }
+    if (Tk.x == T_ZERO) {
+        b.a0 = ns;
+        b.n0 = max(0, pe - ns + 1);
+    } else {
+        const int pa = pos_edge(c, Tk, Ek, x);
+        const int nb = neg_edge(c, Tk, Ek, x);
+        b.a0 = pa;
+        b.n0 = max(0, pe - pa + 1);
+        b.a1 = ns;
+        b.n1 = max(0, nb - ns + 1);
+    }
+    return b;
+}
+
+// Largest |o| a run reaches, for the FAST test.
+__device__ __forceinline__ float run_omax(const LaneC& c, int a, int len) {
+    if (len <= 0) return 0.0f;
+    const float o0 = (float)(a - c.cint) - c.cfrac;
+    return fmaxf(fabsf(o0), fabsf(o0 + (float)(len - 1)));
+}
+
+// Everything a warp needs about pivot ring i.
+struct PivotRing {
+    int i, n_i, s_i;
+    float z_i;
+    double th_i, s_i_d;
+    int rlo;
+    long long pair0;
+};
+
+__device__ __forceinline__ RingCtx ring_ctx(const MapDev& g, const PivotRing& P, int r, long long pr) {
+    RingCtx R;
+    R.first = g.ring_first[r];
+    R.n = g.ring_n[r];
+    R.shift = g.ring_shift[r];
+    R.s_r = g.ring_sf[r];
+    R.A = g.pair_A[pr];
+    R.B = 2.0f * P.z_i * R.s_r;
+    R.step = g.ring_step[r];
+    R.inv_n = g.ring_invn[r];
+    return R;
+}
+
+__device__ __forceinline__ ExactCtx exact_ctx(const MapDev& g, const PivotRing& P, int r) {
+    ExactCtx x;
+    x.th_i = P.th_i;
+    x.th_r = g.ring_th[r];
+    x.s_i = P.s_i_d;
+    x.s_r = g.ring_s[r];
+    x.n_r = g.ring_n[r];
+    return x;
+}
+
+// Accumulate the bin-k moments of ring r into the lane's registers.
+template <int M, bool SELF>
+__device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P, int r, int k, int q,
+                                             const float2* __restrict__ wdw, float (&re)[M + 1],
+                                             float (&im)[M + 1], float& W, float& Q, float& QW) {
+    const long long pr = P.pair0 + (r - P.rlo);
+    const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
+    const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
+    if (Tk.x == T_INF || Tk1.x == T_ZERO) return;  // no bin-k pixel on this ring
+    const RingCtx R = ring_ctx(g, P, r, pr);
+    const ExactCtx x = exact_ctx(g, P, r);
+    const LaneC c = lane_c(q, P.s_i, P.n_i, R.shift, R.n);
+    const bool sym = (R.n == P.n_i) && (Tk1.x != T_INF);
+    const BinRuns b = bin_runs(c, Tk, Tk1, g.E[k], g.E[k + 1], x, R.n, sym);
+    if (sym) {
+        if (b.centre) {  // the pixel straight north or south of the pivot
+            const float2 v = __ldg(wdw + R.first + wrap_idx(c.cint, R.n));
+            float cph, sph;
+            pixel_dir<false>(-c.cfrac, R, cph, sph);
+            harmonics<M>(re, im, cph, sph, v.x, v.x);
+            W += v.y;
+            if (SELF) {
+                Q = fmaf(v.x, v.x, Q);
+                QW = fmaf(v.y, v.y, QW);
+            }
+        }
+        const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
+        if (fast)
+            walk_pairs<M, true, SELF>(R, wdw, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
+        else
+            walk_pairs<M, false, SELF>(R, wdw, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
+        return;
+    }
+    const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
+    const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
+    if (fast) {
+        walk_run<M, true, SELF>(R, wdw, c, b.a0, b.n0, re, im, W, Q, QW);
+        walk_run<M, true, SELF>(R, wdw, c, b.a1, b.n1, re, im, W, Q, QW);
+    } else {
+        walk_run<M, false, SELF>(R, wdw, c, b.a0, b.n0, re, im, W, Q, QW);
+        walk_run<M, false, SELF>(R, wdw, c, b.a1, b.n1, re, im, W, Q, QW);
+    }
+}
+
+// Shared-memory layout of a tile's moments.
+//   A[k][m][2][32] : sum w d cos(m phi), sum w d sin(m phi)   (a = re - i im)
+//   W[k][32], Q[k][32], QW[k][32], piv[2][32] (w d, w of the pivots)
+template <int M>
+__host__ __device__ inline size_t tile_floats(int K) {
+    return (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE + 2 * TILE;
+}
+
+// Load the tile's pivot description; returns false if no lane has w != 0.
+__device__ __forceinline__ PivotRing pivot_ring(const MapDev& g, int i) {
+    PivotRing P;
+    P.i = i;
+    P.n_i = g.ring_n[i];
+    P.s_i = g.ring_shift[i];
+    P.z_i = g.ring_zf[i];
+    P.th_i = g.ring_th[i];
+    P.s_i_d = g.ring_s[i];
+    P.rlo = g.ring_range[i].x;
+    P.pair0 = g.pair_off[i];
+    return P;
+}
+
+// All warps of the CTA: accumulate the moments of the tile into shared memory.
+// Smem must be zeroed beforehand; it is complete after the caller's __syncthreads().
+template <int M, bool SELF>
+__device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P, int q,
+                                             const float2* __restrict__ wdw, float* sA, float* sW,
+                                             float* sQ, float* sQW) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < g.K; ++k) {
+        const int2 br = g.bin_range[(long long)P.i * g.K + k];
+        if (br.x + warp > br.y) continue;
+        float re[M + 1], im[M + 1];
+#pragma unroll
+        for (int m = 0; m <= M; ++m) {
+            re[m] = 0.0f;
+            im[m] = 0.0f;
+        }
+        float W = 0.0f, Q = 0.0f, QW = 0.0f;
+        for (int r = br.x + warp; r <= br.y; r += NWARPS)
+            fwd_ring_bin<M, SELF>(g, P, r, k, q, wdw, re, im, W, Q, QW);
+        float* a = sA + (size_t)k * (M + 1) * 2 * TILE;
+#pragma unroll
+        for (int m = 0; m <= M; ++m) {
+            atomicAdd(a + (2 * m) * TILE + lane, re[m]);
+            atomicAdd(a + (2 * m + 1) * TILE + lane, im[m]);
+        }
+        atomicAdd(sW + k * TILE + lane, W);
+        if (SELF) {
+            atomicAdd(sQ + k * TILE + lane, Q);
+            atomicAdd(sQW + k * TILE + lane, QW);
+        }
+    }
+}
+
+// Per-tile partial sums into the CTA's FP64 slot (eq. zetamEst2 summed over the
+// tile's pivots).  Slot layout: for m, for pair (k1 <= k2): (Re S, Im S); then D for
+// pairs; then sum_i w_i d_i Q^k(i) and sum_i w_i QW^k(i) for k.
+template <int M>
+__device__ __forceinline__ void tile_contract(int K, const float* sA, const float* sW, const float* sQ,
+                                              const float* sQW, const float* sPiv, double* slot,
+                                              bool self) {
+    const int P = n_pairs_tri(K);
+    const int nS = (M + 1) * P;
+    const float* wd = sPiv;
+    const float* wt = sPiv + TILE;
+    for (int e = threadIdx.x; e < nS + P + (self ? K : 0); e += NTHREADS) {
+        if (e < nS) {
+            const int m = e / P;
+            const int pidx = e - m * P;
+            int k2 = (int)((sqrtf(8.0f * pidx + 1.0f) - 1.0f) * 0.5f);
+            while (k2 * (k2 + 1) / 2 > pidx) --k2;
+            while ((k2 + 1) * (k2 + 2) / 2 <= pidx) ++k2;
+            const int k1 = pidx - k2 * (k2 + 1) / 2;
+            const float* r1 = sA + ((size_t)k1 * (M + 1) + m) * 2 * TILE;
+            const float* i1 = r1 + TILE;
+            const float* r2 = sA + ((size_t)k2 * (M + 1) + m) * 2 * TILE;
+            const float* i2 = r2 + TILE;
+            float sr = 0.0f, si = 0.0f;
+            // start each thread at its own lane so a warp's 32 rows hit 32 banks
+#pragma unroll 8
+            for (int j = 0; j < TILE; ++j) {
+                const int l = (j + threadIdx.x) & (TILE - 1);
+                const float a = r1[l], b = i1[l], cc = r2[l], d = i2[l];
+                sr = fmaf(wd[l], fmaf(a, cc, b * d), sr);
+                si = fmaf(wd[l], fmaf(a, d, -b * cc), si);
+            }
+            slot[2 * e] += (double)sr;
+            slot[2 * e + 1] += (double)si;
+        } else if (e < nS + P) {
+            const int pidx = e - nS;
+            int k2 = (int)((sqrtf(8.0f * pidx + 1.0f) - 1.0f) * 0.5f);
+            while (k2 * (k2 + 1) / 2 > pidx) --k2;
+            while ((k2 + 1) * (k2 + 2) / 2 <= pidx) ++k2;
+            const int k1 = pidx - k2 * (k2 + 1) / 2;
+            float s = 0.0f;
+#pragma unroll 8
+            for (int j = 0; j < TILE; ++j) {
+                const int l = (j + threadIdx.x) & (TILE - 1);
+                s = fmaf(wt[l], sW[k1 * TILE + l] * sW[k2 * TILE + l], s);
+            }
+            slot[nS + e] += (double)s;
+        } else {
+            const int k = e - nS - P;
+            float s1 = 0.0f, s2 = 0.0f;
+            for (int j = 0; j < TILE; ++j) {
+                const int l = (j + threadIdx.x) & (TILE - 1);
+                s1 = fmaf(wd[l], sQ[k * TILE + l], s1);
+                s2 = fmaf(wt[l], sQW[k * TILE + l], s2);
+            }
+            slot[2 * nS + P + k] += (double)s1;
+            slot[2 * nS + P + K + k] += (double)s2;
+        }
+    }
+}
+
+template <int M, bool SELF>
+__global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall c) {
+    extern __shared__ float smem[];
+    __shared__ int s_tile;
+    const int K = g.K;
+    float* sA = smem;
+    float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
+    float* sQ = sW + K * TILE;
+    float* sQW = sQ + K * TILE;
+    float* sPiv = sQW + K * TILE;
+    const int lane = threadIdx.x & 31;
+    const size_t nfl = tile_floats<M>(K) - 2 * TILE;
+    double* slot = c.slots + (size_t)blockIdx.x * n_entries(K, M);
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if ((long long)tile >= g.ntiles) break;
+        const int2 tq = g.tiles[tile];
+        if (tq.x < 0 || tq.x >= g.nrings) {
+            if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
+            __syncthreads();
+            continue;
+        }
+        const PivotRing P = pivot_ring(g, tq.x);
+        const int q = tq.y + lane;
+        const long long pix = g.ring_first[P.i] + q;
+        const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+        const float2 pv = in ? c.wdw[pix] : make_float2(0.0f, 0.0f);
+        // lanes past the end of the ring walk the geometry of its last pivot (with zero
+        // weight), which keeps every unwrapped pixel index within [-n_r, 2 n_r)
+        const int qg = min(q, P.n_i - 1);
+        if (!__syncthreads_or(pv.y != 0.0f)) continue;
+        for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
+        if (threadIdx.x < TILE) {
+            sPiv[lane] = pv.x;
+            sPiv[TILE + lane] = pv.y;
+        }
+        __syncthreads();
+        tile_moments<M, SELF>(g, P, qg, c.wdw, sA, sW, sQ, sQW);
+        __syncthreads();
+        tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+        __syncthreads();
+    }
+}
+
+
+// ------------------------------------------------------------- pair count
+#if defined(TPCF_M) && TPCF_M == 0  // one definition, in the M = 0 object
+// counts[0] += in-bin ordered pairs (i, j) of the pivots with w_i != 0 (any w_j);
+// counts[1] += those visited as mirror pairs, counts[2] += those visited singly.
+// Uses the same run construction as the forward, without touching pixel data.
+__global__ void __launch_bounds__(NTHREADS) map_count_kernel(MapDev g, const float2* __restrict__ wdw,
+                                                             long long piv_lo, long long piv_hi,
+                                                             unsigned long long* counts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+        const int2 tq = g.tiles[tile];
+        const PivotRing P = pivot_ring(g, tq.x);
+        const int q = tq.y + lane;
+        const long long pix = g.ring_first[P.i] + q;
+        const bool in = (q < P.n_i) && pix >= piv_lo && pix < piv_hi;
+        const bool live = in && wdw[pix].y != 0.0f;
+        const int qg = min(q, P.n_i - 1);
+        unsigned long long n_sym = 0, n_plain = 0;
+        for (int k = 0; k < g.K; ++k) {
+            const int2 br = g.bin_range[(long long)P.i * g.K + k];
+            for (int r = br.x + warp; r <= br.y; r += NWARPS) {
+                const long long pr = P.pair0 + (r - P.rlo);
+                const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
+                const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
+                if (Tk.x == T_INF || Tk1.x == T_ZERO) continue;
+                const int n_r = g.ring_n[r];
+                const ExactCtx x = exact_ctx(g, P, r);
+                const LaneC c = lane_c(qg, P.s_i, P.n_i, g.ring_shift[r], n_r);
+                const bool sym = (n_r == P.n_i) && (Tk1.x != T_INF);
+                const BinRuns b = bin_runs(c, Tk, Tk1, g.E[k], g.E[k + 1], x, n_r, sym);
+                if (sym) {
+                    n_sym += 2ull * (unsigned long long)b.n0;
+                    n_plain += b.centre ? 1ull : 0ull;
+                } else {
+                    n_plain += (unsigned long long)(b.n0 + b.n1);
+                }
+            }
+        }
+        if (live) {
+            atomicAdd(counts, n_sym + n_plain);
+            atomicAdd(counts + 1, n_sym);
+            atomicAdd(counts + 2, n_plain);
+        }
+    }
+}
+#endif
+
+// ------------------------------------------------------------------ adjoint
+//
+// dL/d d_p for L(zeta), with C_m = (dL/dRe zeta + i dL/dIm zeta) / D and
+// H_m(k,k') = conj(C_m(k,k')) + C_m(k',k) (prepared by the host side):
+//   primary term      w_p * (1/2) sum_{k,m} Re[a_m^k(p) h_m^k(p)]
+//   neighbour legs    w_p * sum_{i: p in nbr(i)} w_i d_i sum_m Re[e^{-i m phi_ip} h_m^{k(ip)}(i)]
+//   with h_m^k(i) = sum_{k'} H_m(k,k') conj(a_m^{k'}(i)).
+// A tile recomputes its a (as the forward), turns it into h in place, then sweeps its
+// neighbour rings again; each warp gathers its ring's contributions in a shared-memory
+// row buffer and flushes the row to the gradient with one atomic add per pixel.
+
+constexpr int ROW = 512;  // floats per warp row buffer (wider rows fall back to whole-ring or global adds)
+
+// val = sum_m (cos(m phi) hr_m + sin(m phi) hi_m): X the cosine part, Y the sine part.
+template <int M>
+__device__ __forceinline__ void adj_harmonics(const float (&hr)[M + 1], const float (&hi)[M + 1], float cph,
+                                              float sph, float& X, float& Y) {
+    X = hr[0];
+    Y = 0.0f;
+    if constexpr (M >= 1) {
+        float t0 = 1.0f, t1 = cph, s0 = 0.0f, s1 = sph;
+        X = fmaf(t1, hr[1], X);
+        Y = s1 * hi[1];
+        const float c2 = cph + cph;
+#pragma unroll
+        for (int m = 2; m <= M; ++m) {
+            const float t2 = fmaf(c2, t1, -t0);
+            const float s2 = fmaf(c2, s1, -s0);
+            X = fmaf(t2, hr[m], X);
+            Y = fmaf(s2, hi[m], Y);
+            t0 = t1;
+            t1 = t2;
+            s0 = s1;
+            s1 = s2;
+        }
+    }
+}
+
+// Where the contribution to pixel p (unwrapped index on ring R) goes.
+struct RowSink {
+    float* buf;     // warp row buffer, or NULL for direct global adds
+    int lo;         // buffer index = p - lo (window mode) ...
+    bool whole;     // ... or = wrap(p) (whole-ring mode)
+    float* grad;    // gradient row base (grad + first of ring)
+    int n;
+};
+
+__device__ __forceinline__ void sink_add(const RowSink& s, int p_unwrapped, int p_wrapped, float v) {
+    if (s.buf) {
+        atomicAdd(s.buf + (s.whole ? p_wrapped : p_unwrapped - s.lo), v);
+    } else {
+        atomicAdd(s.grad + p_wrapped, v);
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void adj_harmonics2(const float (&hr)[M + 1], const float (&hi)[M + 1], float ca,
+                                               float sa, float cb, float sb, float& Xa, float& Ya, float& Xb,
+                                               float& Yb) {
+    Xa = hr[0];
+    Xb = hr[0];
+    Ya = 0.0f;
+    Yb = 0.0f;
+    if constexpr (M >= 1) {
+        float ta0 = 1.0f, ta1 = ca, sa0 = 0.0f, sa1 = sa;
+        float tb0 = 1.0f, tb1 = cb, sb0 = 0.0f, sb1 = sb;
+        Xa = fmaf(ta1, hr[1], Xa);
+        Xb = fmaf(tb1, hr[1], Xb);
+        Ya = sa1 * hi[1];
+        Yb = sb1 * hi[1];
+        const float c2a = ca + ca, c2b = cb + cb;
+#pragma unroll
+        for (int m = 2; m <= M; ++m) {
+            const float ta2 = fmaf(c2a, ta1, -ta0);
+            const float tb2 = fmaf(c2b, tb1, -tb0);
+            const float sa2 = fmaf(c2a, sa1, -sa0);
+            const float sb2 = fmaf(c2b, sb1, -sb0);
+            Xa = fmaf(ta2, hr[m], Xa);
+            Xb = fmaf(tb2, hr[m], Xb);
+            Ya = fmaf(sa2, hi[m], Ya);
+            Yb = fmaf(sb2, hi[m], Yb);
+            ta0 = ta1;
+            ta1 = ta2;
+            tb0 = tb1;
+            tb1 = tb2;
+            sa0 = sa1;
+            sa1 = sa2;
+            sb0 = sb1;
+            sb1 = sb2;
+        }
+    }
+}
+
+template <int M, bool FAST>
+__device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
+                                        int a, int len, const float (&hr)[M + 1], const float (&hi)[M + 1],
+                                        float wdi, const RowSink& s) {
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    const float o0 = (float)(a - c.cint) - c.cfrac;
+    int idx = wrap_idx(a, R.n);
+    const float2* row = wdw + R.first;
+    for (int t = 0; t < maxlen; t += 2) {
+        const bool on0 = t < len, on1 = t + 1 < len;
+        const int idx1 = idx + 1 >= R.n ? idx + 1 - R.n : idx + 1;
+        const float2 v0 = on0 ? __ldg(row + idx) : make_float2(0.0f, 0.0f);
+        const float2 v1 = on1 ? __ldg(row + idx1) : make_float2(0.0f, 0.0f);
+        const float oa = on0 ? o0 + (float)t : o0;
+        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
+        pixel_dir<FAST>(oa, R, ca, sa);
+        pixel_dir<FAST>(ob, R, cb, sb);
+        adj_harmonics2<M>(hr, hi, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
+        if (on0) sink_add(s, a + t, idx, wdi * v0.y * (Xa + Ya));
+        if (on1) sink_add(s, a + t + 1, idx1, wdi * v1.y * (Xb + Yb));
+        idx = idx1 + 1 >= R.n ? idx1 + 1 - R.n : idx1 + 1;
+    }
+}
+
+template <int M, bool FAST>
+__device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
+                                          int a, int len, int mb, const float (&hr)[M + 1],
+                                          const float (&hi)[M + 1], float wdi, const RowSink& s) {
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    const float o0 = (float)(a - c.cint) - c.cfrac;
+    int ip = wrap_idx(a, R.n);
+    int im_ = wrap_idx(mb - a, R.n);
+    const float2* row = wdw + R.first;
+    for (int t = 0; t < maxlen; t += 2) {
+        const bool on0 = t < len, on1 = t + 1 < len;
+        const int ip1 = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
+        const int im1 = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
+        const float2 p0 = on0 ? __ldg(row + ip) : make_float2(0.0f, 0.0f);
+        const float2 m0 = on0 ? __ldg(row + im_) : make_float2(0.0f, 0.0f);
+        const float2 p1 = on1 ? __ldg(row + ip1) : make_float2(0.0f, 0.0f);
+        const float2 m1 = on1 ? __ldg(row + im1) : make_float2(0.0f, 0.0f);
+        const float oa = on0 ? o0 + (float)t : o0;
+        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
+        pixel_dir<FAST>(oa, R, ca, sa);
+        pixel_dir<FAST>(ob, R, cb, sb);
+        adj_harmonics2<M>(hr, hi, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
+        if (on0) {
+            sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya));
+            sink_add(s, mb - a - t, im_, wdi * m0.y * (Xa - Ya));
+        }
+        if (on1) {
+            sink_add(s, a + t + 1, ip1, wdi * p1.y * (Xb + Yb));
+            sink_add(s, mb - a - t - 1, im1, wdi * m1.y * (Xb - Yb));
+        }
+        ip = ip1 + 1 >= R.n ? ip1 + 1 - R.n : ip1 + 1;
+        im_ = im1 - 1 < 0 ? im1 - 1 + R.n : im1 - 1;
+    }
+}
+
+// Neighbour legs of one ring r for the warp's lanes (all bins of r).
+template <int M>
+__device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, int r, int q, float wdi,
+                                         const float2* __restrict__ wdw, const float* sH, float* rowbuf,
+                                         float* grad, int* status) {
+    const int lane = threadIdx.x & 31;
+    const long long pr = P.pair0 + (r - P.rlo);
+    const int2 TK = g.pair_T[pr * (g.K + 1) + g.K];
+    if (TK.x == T_ZERO) return;
+    const RingCtx R = ring_ctx(g, P, r, pr);
+    const ExactCtx x = exact_ctx(g, P, r);
+    const LaneC c = lane_c(q, P.s_i, P.n_i, R.shift, R.n);
+    // row window: every pixel of r within the outer edge of some lane's pivot
+    RowSink s;
+    s.grad = grad + R.first;
+    s.n = R.n;
+    s.whole = false;
+    s.lo = 0;
+    s.buf = rowbuf;
+    int width;
+    {
+        const int clo = __shfl_sync(0xffffffffu, c.cint, 0);
+        const int chi = __shfl_sync(0xffffffffu, c.cint, 31);
+        if (TK.x != T_INF) {
+            s.lo = clo - TK.x - 2;
+            width = chi + TK.x + 3 - s.lo + 1;
+        } else {
+            width = ROW + 1;
+        }
+        if (width > ROW || width >= R.n) {
+            if (R.n <= ROW) {
+                s.whole = true;
+                width = R.n;
+            } else {
+                s.buf = nullptr;
+                width = 0;
+                if (lane == 0) atomicOr(status, ST_ROW_OVERFLOW);
+            }
+        }
+    }
+    for (int e = lane; e < width; e += 32) rowbuf[e] = 0.0f;
+    __syncwarp();
+    for (int k = 0; k < g.K; ++k) {
+        const int2 br = g.bin_range[(long long)P.i * g.K + k];
+        if (r < br.x || r > br.y) continue;
+        const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
+        const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
+        if (Tk.x == T_INF || Tk1.x == T_ZERO) continue;
+        float hr[M + 1], hi[M + 1];
+        const float* hk = sH + (size_t)k * (M + 1) * 2 * TILE;
+#pragma unroll
+        for (int m = 0; m <= M; ++m) {
+            hr[m] = hk[(2 * m) * TILE + lane];
+            hi[m] = hk[(2 * m + 1) * TILE + lane];
+        }
+        const bool sym = (R.n == P.n_i) && (Tk1.x != T_INF);
+        const BinRuns b = bin_runs(c, Tk, Tk1, g.E[k], g.E[k + 1], x, R.n, sym);
+        if (sym) {
+            if (b.centre) {
+                const int p = c.cint;
+                const int pw = wrap_idx(p, R.n);
+                const float2 v = __ldg(wdw + R.first + pw);
+                float cph, sph, X, Y;
+                pixel_dir<false>(-c.cfrac, R, cph, sph);
+                adj_harmonics<M>(hr, hi, cph, sph, X, Y);
+                sink_add(s, p, pw, wdi * v.y * (X + Y));
+            }
+            const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
+            if (fast)
+                adj_pairs<M, true>(R, wdw, c, b.a0, b.n0, b.mb, hr, hi, wdi, s);
+            else
+                adj_pairs<M, false>(R, wdw, c, b.a0, b.n0, b.mb, hr, hi, wdi, s);
+        } else {
+            const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
+            const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
+            if (fast) {
+                adj_run<M, true>(R, wdw, c, b.a0, b.n0, hr, hi, wdi, s);
+                adj_run<M, true>(R, wdw, c, b.a1, b.n1, hr, hi, wdi, s);
+            } else {
+                adj_run<M, false>(R, wdw, c, b.a0, b.n0, hr, hi, wdi, s);
+                adj_run<M, false>(R, wdw, c, b.a1, b.n1, hr, hi, wdi, s);
+            }
+        }
+    }
+    __syncwarp();
+    if (s.buf) {
+        for (int e = lane; e < width; e += 32) {
+            const float v = rowbuf[e];
+            if (v != 0.0f) {
+                const int pw = s.whole ? e : wrap_idx(s.lo + e, R.n);
+                atomicAdd(s.grad + pw, v);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int M>
+__host__ __device__ inline size_t bwd_tile_floats(int K) {
+    return (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE + 2 * TILE + TILE +
+           (size_t)K * K * 2 + (size_t)NWARPS * ROW;
+}
+
+template <int M>
+__global__ void __launch_bounds__(NTHREADS, 2) map_bwd_kernel(MapDev g, MapCall c) {
+    extern __shared__ float smem[];
+    __shared__ int s_tile;
+    const int K = g.K;
+    float* sA = smem;
+    float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
+    float* sQ = sW + K * TILE;
+    float* sQW = sQ + K * TILE;
+    float* sPiv = sQW + K * TILE;
+    float* sPrim = sPiv + 2 * TILE;
+    float* sHm = sPrim + TILE;                  // [K][K][2] one m at a time
+    float* sRow = sHm + (size_t)K * K * 2;      // [NWARPS][ROW]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t nfl = (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if ((long long)tile >= g.ntiles) break;
+        const int2 tq = g.tiles[tile];
+        if (tq.x < 0 || tq.x >= g.nrings) {
+            if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
+            __syncthreads();
+            continue;
+        }
+        const PivotRing P = pivot_ring(g, tq.x);
+        const int q = tq.y + lane;
+        const long long pix = g.ring_first[P.i] + q;
+        const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+        const float2 pv = in ? c.wdw[pix] : make_float2(0.0f, 0.0f);
+        const int qg = min(q, P.n_i - 1);  // see map_fwd_kernel
+        if (!__syncthreads_or(pv.y != 0.0f)) continue;  // no pivot with w != 0: no term
+        for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
+        if (threadIdx.x < TILE) {
+            sPiv[lane] = pv.x;
+            sPiv[TILE + lane] = pv.y;
+            sPrim[lane] = 0.0f;
+        }
+        __syncthreads();
+        // phase 1: the tile's moments, exactly as in the forward
+        tile_moments<M, false>(g, P, qg, c.wdw, sA, sW, sQ, sQW);
+        __syncthreads();
+        // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
+        for (int m = 0; m <= M; ++m) {
+            for (int e = threadIdx.x; e < K * K * 2; e += NTHREADS)
+                sHm[e] = c.H[(size_t)m * K * K * 2 + e];
+            __syncthreads();
+            float hrv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
+            float hiv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
+            int nmine = 0;
+            for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
+                const int k = e / TILE, l = e - k * TILE;
+                float hr = 0.0f, hi = 0.0f;
+                for (int kp = 0; kp < K; ++kp) {
+                    const float Hr = sHm[(k * K + kp) * 2], Hi = sHm[(k * K + kp) * 2 + 1];
+                    const float* ap = sA + ((size_t)kp * (M + 1) + m) * 2 * TILE;
+                    const float tr = ap[l], ti = ap[TILE + l];
+                    hr = fmaf(Hr, tr, fmaf(-Hi, ti, hr));
+                    hi = fmaf(Hr, ti, fmaf(Hi, tr, hi));
+                }
+                const float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+                atomicAdd(sPrim + l, fmaf(ak[l], hr, ak[TILE + l] * hi));
+                hrv[nmine] = hr;
+                hiv[nmine] = hi;
+            }
+            __syncthreads();
+            nmine = 0;
+            for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
+                const int k = e / TILE, l = e - k * TILE;
+                float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+                ak[l] = hrv[nmine];
+                ak[TILE + l] = hiv[nmine];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < TILE && in) {
+            const float gp = 0.5f * pv.y * sPrim[lane];
+            if (gp != 0.0f) atomicAdd(c.grad + pix, gp);
+        }
+        // phase 3: neighbour legs, warps split the neighbour rings
+        const int2 rr = g.ring_range[P.i];
+        for (int r = rr.x + warp; r <= rr.y; r += NWARPS)
+            adj_ring<M>(g, P, r, qg, pv.x, c.wdw, sA, sRow + (size_t)warp * ROW, c.grad, c.status);
+        __syncthreads();
+    }
+}
+
+}  // namespace tpcf

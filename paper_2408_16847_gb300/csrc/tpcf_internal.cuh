@@ -1,0 +1,75 @@
+// Internal declarations shared by the translation units of libtpcf.
+// Device views of plans, launch argument blocks and the per-M launcher table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tpcf.h"
+
+namespace tpcf {
+
+constexpr int TILE = 32;     // pivots per tile: one pivot per lane
+constexpr int NWARPS = 8;    // warps per CTA; they split the neighbour rings of a tile
+constexpr int NTHREADS = TILE * NWARPS;
+
+// Threshold encoding of pair_T entries (see geometry.cu).
+constexpr int T_ZERO = -1;          // every pixel of ring r is at or beyond the edge
+constexpr int T_INF = 0x7fffffff;   // every pixel of ring r is inside the edge
+
+// Read-only device view of a map plan (kernels take it by value).
+struct MapDev {
+    int nside, nrings, K, M;
+    int64_t npix;
+    const int64_t* ring_first;  // [nrings] first pixel of ring
+    const int* ring_n;          // [nrings] pixels in ring (always even)
+    const int* ring_shift;      // [nrings] pixel p of the ring sits at phi = pi (2p + shift) / n
+    const float* ring_zf;       // [nrings] cos(colatitude), fp32
+    const float* ring_sf;       // [nrings] sin(colatitude), fp32
+    const float* ring_step;     // [nrings] pi / n (half longitude step), fp32
+    const float* ring_invn;     // [nrings] 1 / n, fp32
+    const double* ring_th;      // [nrings] colatitude, fp64
+    const double* ring_s;       // [nrings] sin(colatitude), fp64
+    const int2* ring_range;     // [nrings] neighbour rings (rlo, rhi) of pivot ring i
+    const int2* bin_range;      // [nrings * K] rings of pivot ring i that may hold bin-k pixels
+    const int64_t* pair_off;    // [nrings] first (i, r) pair index of pivot ring i
+    const float* pair_A;        // [npairs] sin(theta_i - theta_r), from fp64
+    const int2* pair_T;         // [npairs * (K+1)] edge offsets T_e in ring-r pixels
+    const int2* tiles;          // [ntiles] (ring, first pivot index in ring)
+    int64_t ntiles;
+    const double* E;            // [K+1] sin^2(theta_e / 2)
+};
+
+// Per-call arguments of the map kernels.
+struct MapCall {
+    const float2* wdw;      // [npix] (w * delta, w)
+    int64_t piv_lo, piv_hi; // pivot pixel range
+    double* slots;          // [grid * nentries] per-CTA fp64 partial sums
+    int* counter;           // work counter (zeroed before launch)
+    int* status;            // latched device error flags
+    const float* H;         // backward: [(M+1) * K * K * 2] fp32, conj(C(k,k')) + C(k',k)
+    float* grad;            // backward: [npix]
+    int self_subtract;      // subtract the j = k self term
+};
+
+// Entries of the per-tile partial sums: S for k1 <= k2 (complex), then D (k1 <= k2),
+// then, with self-pair subtraction, the two diagonals sum w d Q and sum w QW.
+inline __host__ __device__ int n_pairs_tri(int K) { return K * (K + 1) / 2; }
+inline __host__ __device__ int n_entries(int K, int M) {
+    return 2 * (M + 1) * n_pairs_tri(K) + n_pairs_tri(K) + 2 * K;
+}
+
+// Device status bits.
+constexpr int ST_BAD_TILE = 1;
+constexpr int ST_ROW_OVERFLOW = 2;
+
+// Launchers generated per M in map_inst.cu (compiled once per TPCF_M value).
+typedef cudaError_t (*map_launch_fn)(const MapDev& g, const MapCall& c, int grid, cudaStream_t s);
+size_t map_fwd_smem(int K, int M);
+size_t map_bwd_smem(int K, int M);
+map_launch_fn map_fwd_launcher(int M);
+map_launch_fn map_bwd_launcher(int M);
+int map_fwd_blocks_per_sm(int M, size_t smem);
+int map_bwd_blocks_per_sm(int M, size_t smem);
+
+}  // namespace tpcf

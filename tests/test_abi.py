@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every entry point include/tpcf.h declares;
+argument validation that needs no GPU returns the documented statuses."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_16847_gb300 import build
+    build()
+    from paper_2408_16847_gb300 import _capi
+    return _capi.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tpcf.h")).read()
+    return sorted(set(re.findall(r"\b(tpcf_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_what_binding_lists():
+    from paper_2408_16847_gb300 import _capi
+    assert _declared() == sorted(_capi.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    from paper_2408_16847_gb300 import _capi
+    for code, name in _capi.STATUS.items():
+        assert lib.tpcf_status_string(code).decode() == name
+
+
+def test_invalid_arguments_need_no_gpu(lib):
+    from paper_2408_16847_gb300 import _capi
+    import numpy as np
+    e = np.array([0.01, 0.02, 0.03])
+    b = _capi.Bins(2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4, 0)
+    h = ctypes.c_void_p()
+    # NULL out pointer, bad nside, bad bins: rejected before any CUDA call
+    assert lib.tpcf_plan_create_map(None, 8, ctypes.byref(b), None) == 1
+    assert lib.tpcf_plan_create_map(ctypes.byref(h), 0, ctypes.byref(b), None) == 1
+    bad = np.array([0.02, 0.01, 0.03])
+    b2 = _capi.Bins(2, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4, 0)
+    assert lib.tpcf_plan_create_map(ctypes.byref(h), 8, ctypes.byref(b2), None) == 1
+    b3 = _capi.Bins(2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 17, 0)
+    assert lib.tpcf_plan_create_map(ctypes.byref(h), 8, ctypes.byref(b3), None) == 1
+    b4 = _capi.Bins(2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4, 1 << 7)
+    assert lib.tpcf_plan_create_map(ctypes.byref(h), 8, ctypes.byref(b4), None) == 1
+    assert lib.tpcf_forward(None, None, None, 0, 0, None, None, None, None) == 1
+    assert lib.tpcf_backward(None, None, None, 0, 0, None, None, None, None) == 1
+    assert lib.tpcf_plan_npoints(None) == -1
+    lib.tpcf_plan_destroy(None)
+    assert h.value is None
