@@ -118,6 +118,29 @@ tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const float* d_w,
                          double* d_sums, void* stream);
 
 /*
+ * The forward above for callers that cannot allocate device memory: programs that
+ * hand all device memory to their own pool allocator at start-up, hot loops that
+ * must not enter the CUDA allocator (cudaMalloc/cudaFree can synchronise the
+ * device), embedders with strict device-memory accounting.  The paper has no
+ * counterpart: this is a library service.
+ *
+ * Same inputs, outputs and pivot range as tpcf_forward (no raw sums).  The call
+ * allocates nothing: it reads d_delta and d_w directly and keeps its partial sums
+ * in a fixed 16 MiB __device__ array that every GPU loading the library holds until
+ * the process exits.  The plan is created beforehand (plan creation does allocate).
+ * The first call on a device looks the array's device address up once; make that
+ * first call before any stream capture.  All calls share the array and each call
+ * clears what must start at zero; calls whose GPU work overlaps (other streams,
+ * host threads or plans at the same time) race on it and must be serialised.
+ * Map plans without self-pair subtraction only (else TPCF_ERR_UNSUPPORTED); a plan
+ * whose per-CTA partial sums (2 (m_max+1) K(K+1)/2 + K(K+1)/2 + 2K doubles) do not
+ * fit is rejected with TPCF_ERR_INVALID_ARG and a message in tpcf_last_error().
+ */
+tpcf_status tpcf_forward_noalloc(tpcf_plan plan, const float* d_delta, const float* d_w,
+                                 int64_t pivot_begin, int64_t pivot_end, double* d_zeta, double* d_norm,
+                                 void* stream);
+
+/*
  * Adjoint: d_grad[p] = dL/d(delta_p) for a real loss L of zeta over the same pivot
  * range, given d_dL_dzeta = dL/dRe(zeta) + i dL/dIm(zeta) (zeta layout) and the
  * normalisation d_norm from the matching forward.  Recomputes the moments a_m^k

@@ -21,7 +21,7 @@ MAX_M = 16
 
 # every exported entry point of include/tpcf.h
 EXPORTS = ["tpcf_status_string", "tpcf_last_error", "tpcf_plan_create_map", "tpcf_plan_create_catalog",
-           "tpcf_plan_npoints", "tpcf_plan_kernel_launches", "tpcf_forward", "tpcf_backward", "tpcf_count_pairs", "tpcf_run_host", "tpcf_batch_create",
+           "tpcf_plan_npoints", "tpcf_plan_kernel_launches", "tpcf_forward", "tpcf_forward_noalloc", "tpcf_backward", "tpcf_count_pairs", "tpcf_run_host", "tpcf_batch_create",
            "tpcf_batch_launch", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync",
            "tpcf_plan_destroy"]
 
@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
     L.tpcf_plan_kernel_launches.argtypes = [_vp]
     L.tpcf_forward.restype = ctypes.c_int
     L.tpcf_forward.argtypes = [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]
+    L.tpcf_forward_noalloc.restype = ctypes.c_int
+    L.tpcf_forward_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]
     L.tpcf_backward.restype = ctypes.c_int
     L.tpcf_backward.argtypes = [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]
     L.tpcf_count_pairs.restype = ctypes.c_int

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "geometry.cuh"
+#include "plan.cuh"
 
 using namespace tpcf;
 
@@ -48,61 +49,13 @@ static const MLaunch kLaunch[TPCF_MAX_M + 1] = {
 
 static thread_local char g_last_error[256] = "";
 
-static tpcf_status cuda_fail(cudaError_t e, const char* where) {
+namespace tpcf {
+tpcf_status cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? TPCF_ERR_OOM : TPCF_ERR_CUDA;
 }
-
-#define TRY_CUDA(call)                                           \
-    do {                                                         \
-        cudaError_t _e = (call);                                 \
-        if (_e != cudaSuccess) return cuda_fail(_e, #call);      \
-    } while (0)
-
-enum PlanKind { PLAN_MAP = 1, PLAN_CATALOG = 2 };
-
-struct tpcf_plan_s {
-    int kind = 0;
-    int device = 0;
-    int num_sms = 0;
-    int64_t npoints = 0;
-    int K = 0, M = 0;
-    uint32_t flags = 0;
-    std::vector<double> edges;
-    std::vector<void*> allocs;  // everything freed by destroy
-    MapDev map{};
-    // per-call scratch
-    float2* wdw = nullptr;
-    double* slots = nullptr;
-    int fwd_grid = 0, bwd_grid = 0;
-    int nent = 0;
-    double* sums = nullptr;
-    int* counter = nullptr;
-    int* status = nullptr;
-    float* H = nullptr;
-    // staging for tpcf_run_host
-    float* st_delta = nullptr;
-    float* st_w = nullptr;
-    double* st_dL = nullptr;
-    double* st_zeta = nullptr;
-    double* st_norm = nullptr;
-    float* st_grad = nullptr;
-    cudaStream_t last_stream = nullptr;
-    long long launches = 0;  // kernels this plan has launched (bookkeeping for benchmarks)
-
-    template <typename T>
-    cudaError_t alloc(T** p, size_t count) {
-        void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
-        if (e != cudaSuccess) return e;
-        allocs.push_back(q);
-        *p = (T*)q;
-        return cudaSuccess;
-    }
-    ~tpcf_plan_s() {
-        for (void* p : allocs) cudaFree(p);
-    }
-};
+void set_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace tpcf
 
 extern "C" const char* tpcf_status_string(tpcf_status s) {
     switch (s) {

@@ -15,12 +15,12 @@ cudaError_t TPCF_CAT(map_fwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c
                                                cudaStream_t s) {
     const size_t smem = tile_floats<TPCF_M>(g.K) * sizeof(float);
     if (c.self_subtract) {
-        auto* k = map_fwd_kernel<TPCF_M, true>;
+        auto* k = map_fwd_kernel<TPCF_M, true, false>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k<<<grid, NTHREADS, smem, s>>>(g, c);
     } else {
-        auto* k = map_fwd_kernel<TPCF_M, false>;
+        auto* k = map_fwd_kernel<TPCF_M, false, false>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k<<<grid, NTHREADS, smem, s>>>(g, c);
@@ -42,13 +42,13 @@ int TPCF_CAT(map_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
     const size_t smem = tile_floats<TPCF_M>(K) * sizeof(float);
     int nb = 0;
     if (self_subtract) {
-        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, true>, NTHREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, true, false>, NTHREADS, smem);
     } else {
-        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, false>, NTHREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, false, false>, NTHREADS, smem);
     }
     return nb;
 }
@@ -59,6 +59,17 @@ int TPCF_CAT(map_bwd_occupancy_m, TPCF_M)(int K) {
     cudaFuncSetAttribute(map_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_bwd_kernel<TPCF_M>, NTHREADS, smem);
     return nb;
+}
+
+// Forward that reads the caller's delta and w directly (no packed copy).
+cudaError_t TPCF_CAT(map_fwd_direct_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid,
+                                                      cudaStream_t s) {
+    const size_t smem = tile_floats<TPCF_M>(g.K) * sizeof(float);
+    auto* k = map_fwd_kernel<TPCF_M, false, true>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(g, c);
+    return cudaGetLastError();
 }
 
 size_t TPCF_CAT(map_fwd_smem_m, TPCF_M)(int K) { return tile_floats<TPCF_M>(K) * sizeof(float); }

@@ -210,21 +210,35 @@ __device__ __forceinline__ int wrap_idx(int p, int n) {
     return p < 0 ? p + n : (p >= n ? p - n : p);
 }
 
+// Neighbour data access: the packed (w d, w) array the library prepares, or the
+// caller's delta and w read directly (used where no packing buffer may be allocated).
+struct PackedLoad {
+    const float2* __restrict__ p;
+    __device__ __forceinline__ float2 operator()(long long i) const { return __ldg(p + i); }
+};
+struct DirectLoad {
+    const float* __restrict__ d;
+    const float* __restrict__ w;
+    __device__ __forceinline__ float2 operator()(long long i) const {
+        const float wi = __ldg(w + i);
+        return make_float2(wi * __ldg(d + i), wi);
+    }
+};
+
 // Walk pixels [a, a + len) of ring R (lane-private run), accumulating into the bin.
 // Two pixels per iteration.
-template <int M, bool FAST, bool SELF>
-__device__ __forceinline__ void walk_run(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
-                                         int a, int len, float (&re)[M + 1], float (&im)[M + 1],
-                                         float& W, float& Q, float& QW) {
+template <int M, bool FAST, bool SELF, class L>
+__device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
+                                         float (&re)[M + 1], float (&im)[M + 1], float& W, float& Q,
+                                         float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float o0 = (float)(a - c.cint) - c.cfrac;
     int idx = wrap_idx(a, R.n);
-    const float2* row = wdw + R.first;
     for (int t = 0; t < maxlen; t += 2) {
         const bool on0 = t < len, on1 = t + 1 < len;
         const int idx1 = idx + 1 >= R.n ? idx + 1 - R.n : idx + 1;
-        const float2 v0 = on0 ? __ldg(row + idx) : make_float2(0.0f, 0.0f);
-        const float2 v1 = on1 ? __ldg(row + idx1) : make_float2(0.0f, 0.0f);
+        const float2 v0 = on0 ? ld(R.first + idx) : make_float2(0.0f, 0.0f);
+        const float2 v1 = on1 ? ld(R.first + idx1) : make_float2(0.0f, 0.0f);
         const float oa = on0 ? o0 + (float)t : o0;
         const float ob = on1 ? o0 + (float)(t + 1) : o0;
         float ca, sa, cb, sb;
@@ -243,24 +257,22 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const float2* __restr
 // Walk the pixel pairs (p, mb - p), p in [a, a + len): mirror images about the
 // pivot's meridian (belt rings with as many pixels as the pivot ring).  Two pairs
 // (four pixels) per iteration.
-template <int M, bool FAST, bool SELF>
-__device__ __forceinline__ void walk_pairs(const RingCtx& R, const float2* __restrict__ wdw,
-                                           const LaneC& c, int a, int len, int mb,
-                                           float (&re)[M + 1], float (&im)[M + 1], float& W, float& Q,
-                                           float& QW) {
+template <int M, bool FAST, bool SELF, class L>
+__device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
+                                           int mb, float (&re)[M + 1], float (&im)[M + 1], float& W,
+                                           float& Q, float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float o0 = (float)(a - c.cint) - c.cfrac;
     int ip = wrap_idx(a, R.n);
     int im_ = wrap_idx(mb - a, R.n);
-    const float2* row = wdw + R.first;
     for (int t = 0; t < maxlen; t += 2) {
         const bool on0 = t < len, on1 = t + 1 < len;
         const int ip1 = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
         const int im1 = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
-        const float2 p0 = on0 ? __ldg(row + ip) : make_float2(0.0f, 0.0f);
-        const float2 m0 = on0 ? __ldg(row + im_) : make_float2(0.0f, 0.0f);
-        const float2 p1 = on1 ? __ldg(row + ip1) : make_float2(0.0f, 0.0f);
-        const float2 m1 = on1 ? __ldg(row + im1) : make_float2(0.0f, 0.0f);
+        const float2 p0 = on0 ? ld(R.first + ip) : make_float2(0.0f, 0.0f);
+        const float2 m0 = on0 ? ld(R.first + im_) : make_float2(0.0f, 0.0f);
+        const float2 p1 = on1 ? ld(R.first + ip1) : make_float2(0.0f, 0.0f);
+        const float2 m1 = on1 ? ld(R.first + im1) : make_float2(0.0f, 0.0f);
         const float oa = on0 ? o0 + (float)t : o0;
         const float ob = on1 ? o0 + (float)(t + 1) : o0;
         float ca, sa, cb, sb;
@@ -370,10 +382,10 @@ __device__ __forceinline__ ExactCtx exact_ctx(const MapDev& g, const PivotRing& 
 }
 
 // Accumulate the bin-k moments of ring r into the lane's registers.
-template <int M, bool SELF>
+template <int M, bool SELF, class L>
 __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P, int r, int k, int q,
-                                             const float2* __restrict__ wdw, float (&re)[M + 1],
-                                             float (&im)[M + 1], float& W, float& Q, float& QW) {
+                                             const L& ld, float (&re)[M + 1], float (&im)[M + 1], float& W,
+                                             float& Q, float& QW) {
     const long long pr = P.pair0 + (r - P.rlo);
     const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
     const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
@@ -385,7 +397,7 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
     const BinRuns b = bin_runs(c, Tk, Tk1, g.E[k], g.E[k + 1], x, R.n, sym);
     if (sym) {
         if (b.centre) {  // the pixel straight north or south of the pivot
-            const float2 v = __ldg(wdw + R.first + wrap_idx(c.cint, R.n));
+            const float2 v = ld(R.first + wrap_idx(c.cint, R.n));
             float cph, sph;
             pixel_dir<false>(-c.cfrac, R, cph, sph);
             harmonics<M>(re, im, cph, sph, v.x, v.x);
@@ -397,19 +409,19 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
         }
         const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
         if (fast)
-            walk_pairs<M, true, SELF>(R, wdw, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
+            walk_pairs<M, true, SELF>(R, ld, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
         else
-            walk_pairs<M, false, SELF>(R, wdw, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
+            walk_pairs<M, false, SELF>(R, ld, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
         return;
     }
     const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
     const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
     if (fast) {
-        walk_run<M, true, SELF>(R, wdw, c, b.a0, b.n0, re, im, W, Q, QW);
-        walk_run<M, true, SELF>(R, wdw, c, b.a1, b.n1, re, im, W, Q, QW);
+        walk_run<M, true, SELF>(R, ld, c, b.a0, b.n0, re, im, W, Q, QW);
+        walk_run<M, true, SELF>(R, ld, c, b.a1, b.n1, re, im, W, Q, QW);
     } else {
-        walk_run<M, false, SELF>(R, wdw, c, b.a0, b.n0, re, im, W, Q, QW);
-        walk_run<M, false, SELF>(R, wdw, c, b.a1, b.n1, re, im, W, Q, QW);
+        walk_run<M, false, SELF>(R, ld, c, b.a0, b.n0, re, im, W, Q, QW);
+        walk_run<M, false, SELF>(R, ld, c, b.a1, b.n1, re, im, W, Q, QW);
     }
 }
 
@@ -437,10 +449,9 @@ __device__ __forceinline__ PivotRing pivot_ring(const MapDev& g, int i) {
 
 // All warps of the CTA: accumulate the moments of the tile into shared memory.
 // Smem must be zeroed beforehand; it is complete after the caller's __syncthreads().
-template <int M, bool SELF>
-__device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P, int q,
-                                             const float2* __restrict__ wdw, float* sA, float* sW,
-                                             float* sQ, float* sQW) {
+template <int M, bool SELF, class L>
+__device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P, int q, const L& ld, float* sA,
+                                             float* sW, float* sQ, float* sQW) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < g.K; ++k) {
         const int2 br = g.bin_range[(long long)P.i * g.K + k];
@@ -453,7 +464,7 @@ __device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P
         }
         float W = 0.0f, Q = 0.0f, QW = 0.0f;
         for (int r = br.x + warp; r <= br.y; r += NWARPS)
-            fwd_ring_bin<M, SELF>(g, P, r, k, q, wdw, re, im, W, Q, QW);
+            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, re, im, W, Q, QW);
         float* a = sA + (size_t)k * (M + 1) * 2 * TILE;
 #pragma unroll
         for (int m = 0; m <= M; ++m) {
@@ -529,7 +540,7 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
     }
 }
 
-template <int M, bool SELF>
+template <int M, bool SELF, bool DIRECT>
 __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall c) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
@@ -558,7 +569,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall 
         const int q = tq.y + lane;
         const long long pix = g.ring_first[P.i] + q;
         const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
-        const float2 pv = in ? c.wdw[pix] : make_float2(0.0f, 0.0f);
+        float2 pv = make_float2(0.0f, 0.0f);
+        if (in) pv = DIRECT ? DirectLoad{c.delta, c.w}(pix) : c.wdw[pix];
         // lanes past the end of the ring walk the geometry of its last pivot (with zero
         // weight), which keeps every unwrapped pixel index within [-n_r, 2 n_r)
         const int qg = min(q, P.n_i - 1);
@@ -569,7 +581,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall 
             sPiv[TILE + lane] = pv.y;
         }
         __syncthreads();
-        tile_moments<M, SELF>(g, P, qg, c.wdw, sA, sW, sQ, sQW);
+        if (DIRECT)
+            tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW);
+        else
+            tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
         __syncthreads();
         tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
         __syncthreads();
@@ -923,7 +938,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_bwd_kernel(MapDev g, MapCall 
         }
         __syncthreads();
         // phase 1: the tile's moments, exactly as in the forward
-        tile_moments<M, false>(g, P, qg, c.wdw, sA, sW, sQ, sQW);
+        tile_moments<M, false>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
         __syncthreads();
         // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
         for (int m = 0; m <= M; ++m) {

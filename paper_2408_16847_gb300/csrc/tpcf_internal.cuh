@@ -43,6 +43,8 @@ struct MapDev {
 // Per-call arguments of the map kernels.
 struct MapCall {
     const float2* wdw;      // [npix] (w * delta, w)
+    const float* delta;     // [npix] caller's delta (kernels that read it directly)
+    const float* w;         // [npix] caller's weights (idem)
     int64_t piv_lo, piv_hi; // pivot pixel range
     double* slots;          // [grid * nentries] per-CTA fp64 partial sums
     int* counter;           // work counter (zeroed before launch)
