@@ -99,7 +99,7 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     int64_t *first, *pair_off, *tile_off, *npairs_r, *ntiles_r, *tot;
     int *npr, *shift;
     double *z, *sd, *th, *E, *theta;
-    float *zf, *sf, *rstep, *rinvn;
+    float *zf, *sf, *sf_lo, *rstep, *rstep_lo, *rinvn, *rinvn_lo;
     int2 *ring_range, *bin_range;
     TRY_CUDA(P->alloc(&first, nrings));
     TRY_CUDA(P->alloc(&npr, nrings));
@@ -111,6 +111,9 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     TRY_CUDA(P->alloc(&sf, nrings));
     TRY_CUDA(P->alloc(&rstep, nrings));
     TRY_CUDA(P->alloc(&rinvn, nrings));
+    TRY_CUDA(P->alloc(&sf_lo, nrings));
+    TRY_CUDA(P->alloc(&rstep_lo, nrings));
+    TRY_CUDA(P->alloc(&rinvn_lo, nrings));
     TRY_CUDA(P->alloc(&ring_range, nrings));
     TRY_CUDA(P->alloc(&bin_range, (size_t)nrings * K));
     TRY_CUDA(P->alloc(&pair_off, nrings));
@@ -123,7 +126,7 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     TRY_CUDA(cudaMemcpyAsync(theta, P->edges.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, s));
     edges_kernel<<<1, 64, 0, s>>>(K, theta, E);
     ring_table_kernel<<<n_blocks(nrings, 128), 128, 0, s>>>((int)nside, nrings, first, npr, shift, z, sd, th,
-                                                            zf, sf, rstep, rinvn);
+                                                            zf, sf, sf_lo, rstep, rstep_lo, rinvn, rinvn_lo);
     ring_range_kernel<<<n_blocks(nrings, 128), 128, 0, s>>>(nrings, K, th, E, npr, ring_range, bin_range,
                                                             npairs_r, ntiles_r);
     exclusive_scan_kernel<<<1, 1024, 0, s>>>(npairs_r, pair_off, nrings, tot);
@@ -133,7 +136,7 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     TRY_CUDA(cudaMemcpyAsync(totals, tot, sizeof(totals), cudaMemcpyDeviceToHost, s));
     TRY_CUDA(cudaStreamSynchronize(s));
     const int64_t npairs = totals[0], ntiles = totals[1];
-    float* pair_A;
+    float2* pair_A;
     int2 *pair_T, *tiles;
     TRY_CUDA(P->alloc(&pair_A, npairs));
     TRY_CUDA(P->alloc(&pair_T, (size_t)npairs * (K + 1)));
@@ -147,6 +150,9 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     g.ring_shift = shift;
     g.ring_zf = zf;
     g.ring_sf = sf;
+    g.ring_sf_lo = sf_lo;
+    g.ring_step_lo = rstep_lo;
+    g.ring_invn_lo = rinvn_lo;
     g.ring_step = rstep;
     g.ring_invn = rinvn;
     g.ring_th = th;

@@ -16,7 +16,8 @@
 namespace tpcf {
 
 __global__ void ring_table_kernel(int nside, int nrings, int64_t* first, int* npr, int* shift, double* z,
-                                  double* s, double* th, float* zf, float* sf, float* step, float* invn) {
+                                  double* s, double* th, float* zf, float* sf, float* sf_lo, float* step,
+                                  float* step_lo, float* invn, float* invn_lo) {
     const int ri = blockIdx.x * blockDim.x + threadIdx.x;
     if (ri >= nrings) return;
     const long long n = nside;
@@ -50,8 +51,12 @@ __global__ void ring_table_kernel(int nside, int nrings, int64_t* first, int* np
     th[ri] = atan2(ss, zz);
     zf[ri] = (float)zz;
     sf[ri] = (float)ss;
-    step[ri] = (float)(M_PI / (double)npr[ri]);
-    invn[ri] = (float)(1.0 / (double)npr[ri]);
+    sf_lo[ri] = (float)(ss - (double)(float)ss);
+    const double st = M_PI / (double)npr[ri], iv = 1.0 / (double)npr[ri];
+    step[ri] = (float)st;
+    step_lo[ri] = (float)(st - (double)(float)st);
+    invn[ri] = (float)iv;
+    invn_lo[ri] = (float)(iv - (double)(float)iv);
 }
 
 // Rings r with sin^2((theta_r - theta_i)/2) < E form a contiguous range around i.
@@ -117,7 +122,7 @@ __global__ void exclusive_scan_kernel(const int64_t* in, int64_t* out, int n, in
 
 __global__ void pair_table_kernel(int nrings, int K, const int64_t* pair_off, int64_t npairs,
                                   const int2* ring_range, const double* th, const double* s, const int* npr,
-                                  const double* E, float* pair_A, int2* pair_T) {
+                                  const double* E, float2* pair_A, int2* pair_T) {
     const int64_t pid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pid >= npairs) return;
     // pivot ring: last i with pair_off[i] <= pid
@@ -128,7 +133,9 @@ __global__ void pair_table_kernel(int nrings, int K, const int64_t* pair_off, in
     }
     const int i = lo;
     const int r = ring_range[i].x + (int)(pid - pair_off[i]);
-    pair_A[pid] = (float)sin(th[i] - th[r]);
+    const double A = sin(th[i] - th[r]);
+    const float A_hi = (float)A;
+    pair_A[pid] = make_float2(A_hi, (float)(A - (double)A_hi));
     const double h = sin(0.5 * (th[r] - th[i]));
     const double f0 = h * h;
     const double sisr = s[i] * s[r];

@@ -6,13 +6,14 @@
 namespace tpcf {
 
 __global__ void ring_table_kernel(int nside, int nrings, int64_t* first, int* npr, int* shift, double* z,
-                                  double* s, double* th, float* zf, float* sf, float* step, float* invn);
+                                  double* s, double* th, float* zf, float* sf, float* sf_lo, float* step,
+                                  float* step_lo, float* invn, float* invn_lo);
 __global__ void ring_range_kernel(int nrings, int K, const double* th, const double* E, const int* npr,
                                   int2* ring_range, int2* bin_range, int64_t* npairs, int64_t* ntiles);
 __global__ void exclusive_scan_kernel(const int64_t* in, int64_t* out, int n, int64_t* total);
 __global__ void pair_table_kernel(int nrings, int K, const int64_t* pair_off, int64_t npairs,
                                   const int2* ring_range, const double* th, const double* s, const int* npr,
-                                  const double* E, float* pair_A, int2* pair_T);
+                                  const double* E, float2* pair_A, int2* pair_T);
 __global__ void tile_list_kernel(int nrings, const int64_t* tile_off, const int64_t* ntiles_ring, int2* tiles);
 __global__ void edges_kernel(int K, const double* theta, double* E);
 

@@ -32,6 +32,7 @@ namespace tpcf {
 
 constexpr float AMBIGUITY = 1.0e-6f;  // > worst fp32 error of the edge position (~1.5e-7 px)
 constexpr float FAST_XMAX = 0.25f;    // |half longitude offset| covered by the polynomial
+constexpr int FLUSH_RINGS = 4;        // rings summed in registers before a shared-memory flush
 
 __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
     long long q = a / b;
@@ -49,6 +50,15 @@ struct LaneC {
 // floor(num / den) from an fp32 estimate corrected in exact integer arithmetic (the
 // estimate is within one of the true quotient for the sizes used here).
 __device__ __forceinline__ LaneC lane_c(int q, int s_i, int n_i, int s_r, int n_r) {
+    if (n_r == n_i) {  // same pixel count: c = q + (s_i - s_r) / 2, no division
+        LaneC c;
+        const int d = s_i - s_r;  // -1, 0 or 1
+        c.cint = q + (d < 0 ? -1 : 0);
+        c.crem = d != 0 ? n_i : 0;
+        c.den = 2 * n_i;
+        c.cfrac = d != 0 ? 0.5f : 0.0f;
+        return c;
+    }
     const long long num = (long long)n_r * (2LL * q + s_i) - (long long)s_r * n_i;
     const int den = 2 * n_i;
     int ci = (int)floorf(__fdividef((float)num, (float)den));
@@ -109,11 +119,11 @@ __device__ __forceinline__ int neg_edge(const LaneC& c, int2 T, double Ee, const
 struct RingCtx {
     long long first;
     int n, shift;
-    float s_r;   // sin(colatitude of r)
-    float A;     // sin(theta_i - theta_r)
-    float B;     // 2 cos(theta_i) sin(theta_r)
-    float step;  // pi / n  (half longitude step)
-    float inv_n; // 1 / n
+    float s_r, s_lo;      // sin(colatitude of r) as an unevaluated fp32 sum s_r + s_lo
+    float A, A_lo;        // sin(theta_i - theta_r), likewise
+    float B;              // 2 cos(theta_i) sin(theta_r)
+    float step, step_lo;  // pi / n (half longitude step) as fp32 hi + lo
+    float inv_n, invn_lo; // 1 / n likewise
 };
 
 // sin x and cos x for |x| <= FAST_XMAX from their Taylor series (truncation error
@@ -130,16 +140,22 @@ __device__ __forceinline__ void sin_cos_series(float x, float& s, float& c) {
 //   east  component  E = s_r sin(2x)
 //   north component  N = sin(theta_i - theta_r) + 2 cos(theta_i) s_r sin^2 x,
 // the cancellation-free form of n_j . e_N(i); phi is measured from north to east.
+// The per-ring constants carry a second fp32 word: their single-fp32 rounding is the
+// same for every pixel of a ring and would shift phi coherently ring by ring.  The
+// offset o = fi - cfrac is passed as its integer part fi (exact in fp32) and the run
+// constants xneg = -cfrac pi/n, uneg = -cfrac/n, so x = pi o / n has one rounding.
 template <bool FAST>
-__device__ __forceinline__ void pixel_dir(float o, const RingCtx& R, float& cph, float& sph) {
+__device__ __forceinline__ void pixel_dir(float fi, float xneg, float uneg, const RingCtx& R, float& cph,
+                                          float& sph) {
     float sx, cx;
     if (FAST) {
-        sin_cos_series(o * R.step, sx, cx);
+        sin_cos_series(fmaf(fi, R.step, fmaf(fi, R.step_lo, xneg)), sx, cx);
     } else {
-        sincospif(o * R.inv_n, &sx, &cx);
+        sincospif(fmaf(fi, R.inv_n, fmaf(fi, R.invn_lo, uneg)), &sx, &cx);
     }
-    const float E = R.s_r * (2.0f * sx * cx);
-    const float N = fmaf(R.B, sx * sx, R.A);
+    const float s2x = 2.0f * sx * cx;
+    const float E = fmaf(R.s_r, s2x, R.s_lo * s2x);
+    const float N = fmaf(R.B, sx * sx, R.A_lo) + R.A;
     // the floor only matters for the masked-out iterations of a run (zero weight),
     // which may sit on the pivot itself; real neighbours have N^2 + E^2 = sin^2 theta.
     const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
@@ -232,18 +248,19 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
                                          float (&re)[M + 1], float (&im)[M + 1], float& W, float& Q,
                                          float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    const float o0 = (float)(a - c.cint) - c.cfrac;
+    const float i0 = (float)(a - c.cint);
+    const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
     int idx = wrap_idx(a, R.n);
     for (int t = 0; t < maxlen; t += 2) {
         const bool on0 = t < len, on1 = t + 1 < len;
         const int idx1 = idx + 1 >= R.n ? idx + 1 - R.n : idx + 1;
         const float2 v0 = on0 ? ld(R.first + idx) : make_float2(0.0f, 0.0f);
         const float2 v1 = on1 ? ld(R.first + idx1) : make_float2(0.0f, 0.0f);
-        const float oa = on0 ? o0 + (float)t : o0;
-        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        const float oa = on0 ? i0 + (float)t : i0;
+        const float ob = on1 ? i0 + (float)(t + 1) : i0;
         float ca, sa, cb, sb;
-        pixel_dir<FAST>(oa, R, ca, sa);
-        pixel_dir<FAST>(ob, R, cb, sb);
+        pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
+        pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
         harmonics2<M>(re, im, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x);
         W += v0.y + v1.y;
         if (SELF) {
@@ -262,7 +279,8 @@ __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const 
                                            int mb, float (&re)[M + 1], float (&im)[M + 1], float& W,
                                            float& Q, float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    const float o0 = (float)(a - c.cint) - c.cfrac;
+    const float i0 = (float)(a - c.cint);
+    const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
     int ip = wrap_idx(a, R.n);
     int im_ = wrap_idx(mb - a, R.n);
     for (int t = 0; t < maxlen; t += 2) {
@@ -273,11 +291,11 @@ __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const 
         const float2 m0 = on0 ? ld(R.first + im_) : make_float2(0.0f, 0.0f);
         const float2 p1 = on1 ? ld(R.first + ip1) : make_float2(0.0f, 0.0f);
         const float2 m1 = on1 ? ld(R.first + im1) : make_float2(0.0f, 0.0f);
-        const float oa = on0 ? o0 + (float)t : o0;
-        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        const float oa = on0 ? i0 + (float)t : i0;
+        const float ob = on1 ? i0 + (float)(t + 1) : i0;
         float ca, sa, cb, sb;
-        pixel_dir<FAST>(oa, R, ca, sa);
-        pixel_dir<FAST>(ob, R, cb, sb);
+        pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
+        pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
         harmonics2<M>(re, im, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x);
         W += (p0.y + m0.y) + (p1.y + m1.y);
         if (SELF) {
@@ -364,10 +382,15 @@ __device__ __forceinline__ RingCtx ring_ctx(const MapDev& g, const PivotRing& P,
     R.n = g.ring_n[r];
     R.shift = g.ring_shift[r];
     R.s_r = g.ring_sf[r];
-    R.A = g.pair_A[pr];
+    R.s_lo = g.ring_sf_lo[r];
+    const float2 Ap = g.pair_A[pr];
+    R.A = Ap.x;
+    R.A_lo = Ap.y;
     R.B = 2.0f * P.z_i * R.s_r;
     R.step = g.ring_step[r];
+    R.step_lo = g.ring_step_lo[r];
     R.inv_n = g.ring_invn[r];
+    R.invn_lo = g.ring_invn_lo[r];
     return R;
 }
 
@@ -399,7 +422,7 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
         if (b.centre) {  // the pixel straight north or south of the pivot
             const float2 v = ld(R.first + wrap_idx(c.cint, R.n));
             float cph, sph;
-            pixel_dir<false>(-c.cfrac, R, cph, sph);
+            pixel_dir<false>(0.0f, 0.0f, -c.cfrac * R.inv_n, R, cph, sph);
             harmonics<M>(re, im, cph, sph, v.x, v.x);
             W += v.y;
             if (SELF) {
@@ -463,18 +486,30 @@ __device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P
             im[m] = 0.0f;
         }
         float W = 0.0f, Q = 0.0f, QW = 0.0f;
-        for (int r = br.x + warp; r <= br.y; r += NWARPS)
-            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, re, im, W, Q, QW);
         float* a = sA + (size_t)k * (M + 1) * 2 * TILE;
+        // Blocked summation: the registers sum FLUSH_RINGS rings, then the block is
+        // added into shared memory, which keeps the running sums short.
+        int nr = 0;
+        for (int r = br.x + warp; r <= br.y; r += NWARPS) {
+            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, re, im, W, Q, QW);
+            if (++nr == FLUSH_RINGS || r + NWARPS > br.y) {
+                nr = 0;
 #pragma unroll
-        for (int m = 0; m <= M; ++m) {
-            atomicAdd(a + (2 * m) * TILE + lane, re[m]);
-            atomicAdd(a + (2 * m + 1) * TILE + lane, im[m]);
-        }
-        atomicAdd(sW + k * TILE + lane, W);
-        if (SELF) {
-            atomicAdd(sQ + k * TILE + lane, Q);
-            atomicAdd(sQW + k * TILE + lane, QW);
+                for (int m = 0; m <= M; ++m) {
+                    atomicAdd(a + (2 * m) * TILE + lane, re[m]);
+                    atomicAdd(a + (2 * m + 1) * TILE + lane, im[m]);
+                    re[m] = 0.0f;
+                    im[m] = 0.0f;
+                }
+                atomicAdd(sW + k * TILE + lane, W);
+                W = 0.0f;
+                if (SELF) {
+                    atomicAdd(sQ + k * TILE + lane, Q);
+                    atomicAdd(sQW + k * TILE + lane, QW);
+                    Q = 0.0f;
+                    QW = 0.0f;
+                }
+            }
         }
     }
 }
@@ -737,7 +772,8 @@ __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restri
                                         int a, int len, const float (&hr)[M + 1], const float (&hi)[M + 1],
                                         float wdi, const RowSink& s) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    const float o0 = (float)(a - c.cint) - c.cfrac;
+    const float i0 = (float)(a - c.cint);
+    const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
     int idx = wrap_idx(a, R.n);
     const float2* row = wdw + R.first;
     for (int t = 0; t < maxlen; t += 2) {
@@ -745,11 +781,11 @@ __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restri
         const int idx1 = idx + 1 >= R.n ? idx + 1 - R.n : idx + 1;
         const float2 v0 = on0 ? __ldg(row + idx) : make_float2(0.0f, 0.0f);
         const float2 v1 = on1 ? __ldg(row + idx1) : make_float2(0.0f, 0.0f);
-        const float oa = on0 ? o0 + (float)t : o0;
-        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        const float oa = on0 ? i0 + (float)t : i0;
+        const float ob = on1 ? i0 + (float)(t + 1) : i0;
         float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
-        pixel_dir<FAST>(oa, R, ca, sa);
-        pixel_dir<FAST>(ob, R, cb, sb);
+        pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
+        pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
         adj_harmonics2<M>(hr, hi, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
         if (on0) sink_add(s, a + t, idx, wdi * v0.y * (Xa + Ya));
         if (on1) sink_add(s, a + t + 1, idx1, wdi * v1.y * (Xb + Yb));
@@ -762,7 +798,8 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
                                           int a, int len, int mb, const float (&hr)[M + 1],
                                           const float (&hi)[M + 1], float wdi, const RowSink& s) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    const float o0 = (float)(a - c.cint) - c.cfrac;
+    const float i0 = (float)(a - c.cint);
+    const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
     int ip = wrap_idx(a, R.n);
     int im_ = wrap_idx(mb - a, R.n);
     const float2* row = wdw + R.first;
@@ -774,11 +811,11 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
         const float2 m0 = on0 ? __ldg(row + im_) : make_float2(0.0f, 0.0f);
         const float2 p1 = on1 ? __ldg(row + ip1) : make_float2(0.0f, 0.0f);
         const float2 m1 = on1 ? __ldg(row + im1) : make_float2(0.0f, 0.0f);
-        const float oa = on0 ? o0 + (float)t : o0;
-        const float ob = on1 ? o0 + (float)(t + 1) : o0;
+        const float oa = on0 ? i0 + (float)t : i0;
+        const float ob = on1 ? i0 + (float)(t + 1) : i0;
         float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
-        pixel_dir<FAST>(oa, R, ca, sa);
-        pixel_dir<FAST>(ob, R, cb, sb);
+        pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
+        pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
         adj_harmonics2<M>(hr, hi, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
         if (on0) {
             sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya));
@@ -856,7 +893,7 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
                 const int pw = wrap_idx(p, R.n);
                 const float2 v = __ldg(wdw + R.first + pw);
                 float cph, sph, X, Y;
-                pixel_dir<false>(-c.cfrac, R, cph, sph);
+                pixel_dir<false>(0.0f, 0.0f, -c.cfrac * R.inv_n, R, cph, sph);
                 adj_harmonics<M>(hr, hi, cph, sph, X, Y);
                 sink_add(s, p, pw, wdi * v.y * (X + Y));
             }

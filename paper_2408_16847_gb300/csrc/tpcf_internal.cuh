@@ -25,15 +25,18 @@ struct MapDev {
     const int* ring_n;          // [nrings] pixels in ring (always even)
     const int* ring_shift;      // [nrings] pixel p of the ring sits at phi = pi (2p + shift) / n
     const float* ring_zf;       // [nrings] cos(colatitude), fp32
-    const float* ring_sf;       // [nrings] sin(colatitude), fp32
+    const float* ring_sf;       // [nrings] sin(colatitude), fp32 (rounded)
+    const float* ring_sf_lo;    // [nrings] sin(colatitude) - ring_sf
     const float* ring_step;     // [nrings] pi / n (half longitude step), fp32
+    const float* ring_step_lo;  // [nrings] pi / n - ring_step
     const float* ring_invn;     // [nrings] 1 / n, fp32
+    const float* ring_invn_lo;  // [nrings] 1 / n - ring_invn
     const double* ring_th;      // [nrings] colatitude, fp64
     const double* ring_s;       // [nrings] sin(colatitude), fp64
     const int2* ring_range;     // [nrings] neighbour rings (rlo, rhi) of pivot ring i
     const int2* bin_range;      // [nrings * K] rings of pivot ring i that may hold bin-k pixels
     const int64_t* pair_off;    // [nrings] first (i, r) pair index of pivot ring i
-    const float* pair_A;        // [npairs] sin(theta_i - theta_r), from fp64
+    const float2* pair_A;       // [npairs] sin(theta_i - theta_r) as fp32 (hi, lo) from fp64
     const int2* pair_T;         // [npairs * (K+1)] edge offsets T_e in ring-r pixels
     const int2* tiles;          // [ntiles] (ring, first pivot index in ring)
     int64_t ntiles;
