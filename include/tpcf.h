@@ -171,11 +171,27 @@ tpcf_status tpcf_run_host(tpcf_plan plan, const float* h_delta, const float* h_w
                           float* h_grad, void* stream);
 
 /*
- * Batched execution for n map plans (mixed nside, bins and m_max): one persistent
- * launch runs every plan's forward tiles from a shared work queue, one launch
- * normalises, and, when d_dL_dzeta[i] != NULL for all i, one persistent launch
- * runs every adjoint.  tpcf_batch_create records the sequence into a CUDA graph
- * (the pointers are baked in); tpcf_batch_launch replays it on `stream`.
+ * Batched execution (Sec. 3 estimator, for n independent maps): n map plans of any
+ * mix of nside, bins and m_max, each with its own inputs and outputs, run as one
+ * short launch sequence whose length does not depend on n.  One persistent pair
+ * kernel per distinct (m_max, self-pair mode) runs the forward tiles of all its
+ * plans from a shared work queue; the small per-entry kernels take every plan in
+ * one launch.  When d_dL_dzeta != NULL the batch also runs the adjoint (every
+ * d_dL_dzeta[i] and d_grad[i] must then be set; not with self-pair subtraction).
+ *
+ * tpcf_batch_create validates the arguments, synchronises the plans' last streams
+ * and records the sequence into a CUDA graph: the pointers are baked in, so the
+ * buffers and plans must outlive the batch.  A plan may appear once per batch, and
+ * its batch and its single calls must not run concurrently (they share the plan's
+ * scratch).  Arrays: plans, d_delta, d_w (float32[npix] each), d_zeta
+ * (double[(m_max+1) K K 2]), d_norm (double[K K]), d_dL_dzeta (same shape as
+ * zeta), d_grad (float[npix], overwritten): host arrays of n device pointers.
+ * Errors: INVALID_ARG (NULL, n outside [1, 256], duplicate plan), UNSUPPORTED
+ * (catalogue plan, adjoint with self-pair subtraction), CUDA/OOM.
+ *
+ * tpcf_batch_launch replays the graph on `stream` (asynchronous; tpcf_plan_sync on
+ * any member reports device errors).  tpcf_batch_kernel_launches gives the kernels
+ * of one replay.  tpcf_batch_destroy synchronises and frees (NULL is a no-op).
  */
 tpcf_status tpcf_batch_create(tpcf_batch* out, const tpcf_plan* plans, int32_t n,
                               const float* const* d_delta, const float* const* d_w,
@@ -183,6 +199,7 @@ tpcf_status tpcf_batch_create(tpcf_batch* out, const tpcf_plan* plans, int32_t n
                               const double* const* d_dL_dzeta, float* const* d_grad,
                               void* stream);
 tpcf_status tpcf_batch_launch(tpcf_batch batch, void* stream);
+int64_t tpcf_batch_kernel_launches(tpcf_batch batch);
 void tpcf_batch_destroy(tpcf_batch batch);
 
 /* Convenience: create, launch once and destroy a batch. */

@@ -22,7 +22,7 @@ MAX_M = 16
 # every exported entry point of include/tpcf.h
 EXPORTS = ["tpcf_status_string", "tpcf_last_error", "tpcf_plan_create_map", "tpcf_plan_create_catalog",
            "tpcf_plan_npoints", "tpcf_plan_kernel_launches", "tpcf_forward", "tpcf_forward_noalloc", "tpcf_backward", "tpcf_count_pairs", "tpcf_run_host", "tpcf_batch_create",
-           "tpcf_batch_launch", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync",
+           "tpcf_batch_launch", "tpcf_batch_kernel_launches", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync",
            "tpcf_plan_destroy"]
 
 
@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]
     L.tpcf_batch_launch.restype = ctypes.c_int
     L.tpcf_batch_launch.argtypes = [_vp, _vp]
+    L.tpcf_batch_kernel_launches.restype = _i64
+    L.tpcf_batch_kernel_launches.argtypes = [_vp]
     L.tpcf_batch_destroy.restype = None
     L.tpcf_batch_destroy.argtypes = [_vp]
     L.tpcf_forward_batched.restype = ctypes.c_int

@@ -386,39 +386,3 @@ extern "C" void tpcf_plan_destroy(tpcf_plan plan) {
     cudaStreamSynchronize(plan->last_stream);
     delete plan;
 }
-
-// ------------------------------------------------------------------- batches
-
-struct tpcf_batch_s {
-    int dummy;
-};
-
-extern "C" tpcf_status tpcf_batch_create(tpcf_batch* out, const tpcf_plan* plans, int32_t n,
-                                         const float* const* d_delta, const float* const* d_w,
-                                         double* const* d_zeta, double* const* d_norm,
-                                         const double* const* d_dL_dzeta, float* const* d_grad, void* stream) {
-    (void)plans; (void)n; (void)d_delta; (void)d_w; (void)d_zeta; (void)d_norm; (void)d_dL_dzeta;
-    (void)d_grad; (void)stream;
-    if (out) *out = nullptr;
-    return TPCF_ERR_UNSUPPORTED;
-}
-
-extern "C" tpcf_status tpcf_batch_launch(tpcf_batch batch, void* stream) {
-    (void)batch;
-    (void)stream;
-    return TPCF_ERR_UNSUPPORTED;
-}
-
-extern "C" void tpcf_batch_destroy(tpcf_batch batch) { delete batch; }
-
-extern "C" tpcf_status tpcf_forward_batched(const tpcf_plan* plans, int32_t n, const float* const* d_delta,
-                                            const float* const* d_w, double* const* d_zeta,
-                                            double* const* d_norm, const double* const* d_dL_dzeta,
-                                            float* const* d_grad, void* stream) {
-    tpcf_batch b = nullptr;
-    tpcf_status st = tpcf_batch_create(&b, plans, n, d_delta, d_w, d_zeta, d_norm, d_dL_dzeta, d_grad, stream);
-    if (st != TPCF_OK) return st;
-    st = tpcf_batch_launch(b, stream);
-    tpcf_batch_destroy(b);
-    return st;
-}

@@ -25,4 +25,27 @@ __global__ void finalize_kernel(const double* sums, int K, int M, int self_subtr
 __global__ void adjoint_prep_kernel(const double* dL_dzeta, const double* norm, int K, int M, float* H);
 __global__ void zero_f32_kernel(float* p, int64_t n);
 
+// Per-plan arguments of the batched small kernels (device-resident array, one entry
+// per plan of a batch).
+struct BatchIO {
+    const float* delta;
+    const float* w;
+    float2* wdw;
+    int64_t npix;
+    double* slots;  // nslots x nent
+    int nslots, nent;
+    double* sums;   // nent
+    int K, M, self_subtract;
+    double* zeta;
+    double* norm;
+    const double* dL;  // NULL without adjoint
+    float* H;
+    float* grad;       // NULL without adjoint
+};
+__global__ void batch_pack_kernel(const BatchIO* io);
+__global__ void batch_zero_kernel(const BatchIO* io, int with_grad);
+__global__ void batch_reduce_kernel(const BatchIO* io);
+__global__ void batch_finalize_kernel(const BatchIO* io);
+__global__ void batch_adjoint_prep_kernel(const BatchIO* io);
+
 }  // namespace tpcf

@@ -75,6 +75,55 @@ cudaError_t TPCF_CAT(map_fwd_direct_launch_m, TPCF_M)(const MapDev& g, const Map
 size_t TPCF_CAT(map_fwd_smem_m, TPCF_M)(int K) { return tile_floats<TPCF_M>(K) * sizeof(float); }
 size_t TPCF_CAT(map_bwd_smem_m, TPCF_M)(int K) { return bwd_tile_floats<TPCF_M>(K) * sizeof(float); }
 
+// Batched forward / adjoint over the plans of a batch that share this M (the
+// dynamic shared memory is the largest any of them needs).
+cudaError_t TPCF_CAT(batch_fwd_launch_m, TPCF_M)(const BatchItem* items, int n, long long total,
+                                                 unsigned long long* counter, int self_subtract, size_t smem,
+                                                 int grid, cudaStream_t s) {
+    if (self_subtract) {
+        auto* k = batch_fwd_kernel<TPCF_M, true>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
+    } else {
+        auto* k = batch_fwd_kernel<TPCF_M, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t TPCF_CAT(batch_bwd_launch_m, TPCF_M)(const BatchItem* items, int n, long long total,
+                                                 unsigned long long* counter, size_t smem, int grid,
+                                                 cudaStream_t s) {
+    auto* k = batch_bwd_kernel<TPCF_M>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
+    return cudaGetLastError();
+}
+
+int TPCF_CAT(batch_fwd_occupancy_m, TPCF_M)(size_t smem, int self_subtract) {
+    int nb = 0;
+    if (self_subtract) {
+        cudaFuncSetAttribute(batch_fwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fwd_kernel<TPCF_M, true>, NTHREADS, smem);
+    } else {
+        cudaFuncSetAttribute(batch_fwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fwd_kernel<TPCF_M, false>, NTHREADS, smem);
+    }
+    return nb;
+}
+
+int TPCF_CAT(batch_bwd_occupancy_m, TPCF_M)(size_t smem) {
+    int nb = 0;
+    cudaFuncSetAttribute(batch_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_bwd_kernel<TPCF_M>, NTHREADS, smem);
+    return nb;
+}
+
 #if TPCF_M == 0
 cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi,
                              unsigned long long* counts, int grid, cudaStream_t s) {

@@ -575,10 +575,10 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
     }
 }
 
+// One forward tile: the moments of its 32 pivots, then their partial sums added to
+// the CTA's slot.  Called by every thread of the CTA (contains barriers).
 template <int M, bool SELF, bool DIRECT>
-__global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall c) {
-    extern __shared__ float smem[];
-    __shared__ int s_tile;
+__device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem) {
     const int K = g.K;
     float* sA = smem;
     float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
@@ -587,45 +587,77 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall 
     float* sPiv = sQW + K * TILE;
     const int lane = threadIdx.x & 31;
     const size_t nfl = tile_floats<M>(K) - 2 * TILE;
-    double* slot = c.slots + (size_t)blockIdx.x * n_entries(K, M);
+    const int2 tq = g.tiles[tile];
+    if (tq.x < 0 || tq.x >= g.nrings) {
+        if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
+        __syncthreads();
+        return;
+    }
+    const PivotRing P = pivot_ring(g, tq.x);
+    const int q = tq.y + lane;
+    const long long pix = g.ring_first[P.i] + q;
+    const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+    float2 pv = make_float2(0.0f, 0.0f);
+    if (in) pv = DIRECT ? DirectLoad{c.delta, c.w}(pix) : c.wdw[pix];
+    // lanes past the end of the ring walk the geometry of its last pivot (with zero
+    // weight), which keeps every unwrapped pixel index within [-n_r, 2 n_r)
+    const int qg = min(q, P.n_i - 1);
+    if (!__syncthreads_or(pv.y != 0.0f)) return;
+    for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
+    if (threadIdx.x < TILE) {
+        sPiv[lane] = pv.x;
+        sPiv[TILE + lane] = pv.y;
+    }
+    __syncthreads();
+    if (DIRECT)
+        tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW);
+    else
+        tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
+    __syncthreads();
+    tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+    __syncthreads();
+}
 
+template <int M, bool SELF, bool DIRECT>
+__global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall c) {
+    extern __shared__ float smem[];
+    __shared__ int s_tile;
+    double* slot = c.slots + (size_t)blockIdx.x * n_entries(g.K, M);
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
         __syncthreads();
         const int tile = s_tile;
         if ((long long)tile >= g.ntiles) break;
-        const int2 tq = g.tiles[tile];
-        if (tq.x < 0 || tq.x >= g.nrings) {
-            if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
-            __syncthreads();
-            continue;
-        }
-        const PivotRing P = pivot_ring(g, tq.x);
-        const int q = tq.y + lane;
-        const long long pix = g.ring_first[P.i] + q;
-        const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
-        float2 pv = make_float2(0.0f, 0.0f);
-        if (in) pv = DIRECT ? DirectLoad{c.delta, c.w}(pix) : c.wdw[pix];
-        // lanes past the end of the ring walk the geometry of its last pivot (with zero
-        // weight), which keeps every unwrapped pixel index within [-n_r, 2 n_r)
-        const int qg = min(q, P.n_i - 1);
-        if (!__syncthreads_or(pv.y != 0.0f)) continue;
-        for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
-        if (threadIdx.x < TILE) {
-            sPiv[lane] = pv.x;
-            sPiv[TILE + lane] = pv.y;
-        }
-        __syncthreads();
-        if (DIRECT)
-            tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW);
-        else
-            tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
-        __syncthreads();
-        tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
-        __syncthreads();
+        fwd_tile<M, SELF, DIRECT>(g, c, tile, slot, smem);
     }
 }
 
+// Batched forward over the plans of a batch that share M: one work queue over the
+// concatenated tiles of all its plans (plan-major); each CTA adds into that plan's
+// slot number blockIdx.x.
+template <int M, bool SELF>
+__global__ void __launch_bounds__(NTHREADS, 2) batch_fwd_kernel(const BatchItem* __restrict__ items, int n,
+                                                               long long total, unsigned long long* counter) {
+    extern __shared__ float smem[];
+    __shared__ long long s_t;
+    __shared__ long long s_first[TPCF_MAX_BATCH + 1];
+    for (int i = threadIdx.x; i <= n; i += NTHREADS) s_first[i] = i < n ? items[i].tile0 : total;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long t = s_t;
+        if (t >= total) break;
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (s_first[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const BatchItem& it = items[lo];
+        double* slot = it.c.slots + (size_t)blockIdx.x * n_entries(it.g.K, M);
+        fwd_tile<M, SELF, false>(it.g, it.c, (int)(t - s_first[lo]), slot, smem);
+    }
+}
 
 // ------------------------------------------------------------- pair count
 #if defined(TPCF_M) && TPCF_M == 0  // one definition, in the M = 0 object
@@ -933,10 +965,9 @@ __host__ __device__ inline size_t bwd_tile_floats(int K) {
            (size_t)K * K * 2 + (size_t)NWARPS * ROW;
 }
 
+// One adjoint tile (all three phases).  Called by every thread of the CTA.
 template <int M>
-__global__ void __launch_bounds__(NTHREADS, 2) map_bwd_kernel(MapDev g, MapCall c) {
-    extern __shared__ float smem[];
-    __shared__ int s_tile;
+__device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int tile, float* smem) {
     const int K = g.K;
     float* sA = smem;
     float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
@@ -949,76 +980,105 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_bwd_kernel(MapDev g, MapCall 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t nfl = (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE;
 
+    const int2 tq = g.tiles[tile];
+    if (tq.x < 0 || tq.x >= g.nrings) {
+        if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
+        __syncthreads();
+        return;
+    }
+    const PivotRing P = pivot_ring(g, tq.x);
+    const int q = tq.y + lane;
+    const long long pix = g.ring_first[P.i] + q;
+    const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+    const float2 pv = in ? c.wdw[pix] : make_float2(0.0f, 0.0f);
+    const int qg = min(q, P.n_i - 1);  // see map_fwd_kernel
+    if (!__syncthreads_or(pv.y != 0.0f)) return;  // no pivot with w != 0: no term
+    for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
+    if (threadIdx.x < TILE) {
+        sPiv[lane] = pv.x;
+        sPiv[TILE + lane] = pv.y;
+        sPrim[lane] = 0.0f;
+    }
+    __syncthreads();
+    // phase 1: the tile's moments, exactly as in the forward
+    tile_moments<M, false>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
+    __syncthreads();
+    // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
+    for (int m = 0; m <= M; ++m) {
+        for (int e = threadIdx.x; e < K * K * 2; e += NTHREADS)
+            sHm[e] = c.H[(size_t)m * K * K * 2 + e];
+        __syncthreads();
+        float hrv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
+        float hiv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
+        int nmine = 0;
+        for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
+            const int k = e / TILE, l = e - k * TILE;
+            float hr = 0.0f, hi = 0.0f;
+            for (int kp = 0; kp < K; ++kp) {
+                const float Hr = sHm[(k * K + kp) * 2], Hi = sHm[(k * K + kp) * 2 + 1];
+                const float* ap = sA + ((size_t)kp * (M + 1) + m) * 2 * TILE;
+                const float tr = ap[l], ti = ap[TILE + l];
+                hr = fmaf(Hr, tr, fmaf(-Hi, ti, hr));
+                hi = fmaf(Hr, ti, fmaf(Hi, tr, hi));
+            }
+            const float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+            atomicAdd(sPrim + l, fmaf(ak[l], hr, ak[TILE + l] * hi));
+            hrv[nmine] = hr;
+            hiv[nmine] = hi;
+        }
+        __syncthreads();
+        nmine = 0;
+        for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
+            const int k = e / TILE, l = e - k * TILE;
+            float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+            ak[l] = hrv[nmine];
+            ak[TILE + l] = hiv[nmine];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < TILE && in) {
+        const float gp = 0.5f * pv.y * sPrim[lane];
+        if (gp != 0.0f) atomicAdd(c.grad + pix, gp);
+    }
+    // phase 3: neighbour legs, warps split the neighbour rings
+    const int2 rr = g.ring_range[P.i];
+    for (int r = rr.x + warp; r <= rr.y; r += NWARPS)
+        adj_ring<M>(g, P, r, qg, pv.x, c.wdw, sA, sRow + (size_t)warp * ROW, c.grad, c.status);
+    __syncthreads();
+}
+
+template <int M>
+__global__ void __launch_bounds__(NTHREADS, 2) map_bwd_kernel(MapDev g, MapCall c) {
+    extern __shared__ float smem[];
+    __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
         __syncthreads();
         const int tile = s_tile;
         if ((long long)tile >= g.ntiles) break;
-        const int2 tq = g.tiles[tile];
-        if (tq.x < 0 || tq.x >= g.nrings) {
-            if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
-            __syncthreads();
-            continue;
-        }
-        const PivotRing P = pivot_ring(g, tq.x);
-        const int q = tq.y + lane;
-        const long long pix = g.ring_first[P.i] + q;
-        const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
-        const float2 pv = in ? c.wdw[pix] : make_float2(0.0f, 0.0f);
-        const int qg = min(q, P.n_i - 1);  // see map_fwd_kernel
-        if (!__syncthreads_or(pv.y != 0.0f)) continue;  // no pivot with w != 0: no term
-        for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
-        if (threadIdx.x < TILE) {
-            sPiv[lane] = pv.x;
-            sPiv[TILE + lane] = pv.y;
-            sPrim[lane] = 0.0f;
-        }
+        bwd_tile<M>(g, c, tile, smem);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(NTHREADS, 2) batch_bwd_kernel(const BatchItem* __restrict__ items, int n,
+                                                               long long total, unsigned long long* counter) {
+    extern __shared__ float smem[];
+    __shared__ long long s_t;
+    __shared__ long long s_first[TPCF_MAX_BATCH + 1];
+    for (int i = threadIdx.x; i <= n; i += NTHREADS) s_first[i] = i < n ? items[i].tile0 : total;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
-        // phase 1: the tile's moments, exactly as in the forward
-        tile_moments<M, false>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
-        __syncthreads();
-        // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
-        for (int m = 0; m <= M; ++m) {
-            for (int e = threadIdx.x; e < K * K * 2; e += NTHREADS)
-                sHm[e] = c.H[(size_t)m * K * K * 2 + e];
-            __syncthreads();
-            float hrv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
-            float hiv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
-            int nmine = 0;
-            for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
-                const int k = e / TILE, l = e - k * TILE;
-                float hr = 0.0f, hi = 0.0f;
-                for (int kp = 0; kp < K; ++kp) {
-                    const float Hr = sHm[(k * K + kp) * 2], Hi = sHm[(k * K + kp) * 2 + 1];
-                    const float* ap = sA + ((size_t)kp * (M + 1) + m) * 2 * TILE;
-                    const float tr = ap[l], ti = ap[TILE + l];
-                    hr = fmaf(Hr, tr, fmaf(-Hi, ti, hr));
-                    hi = fmaf(Hr, ti, fmaf(Hi, tr, hi));
-                }
-                const float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
-                atomicAdd(sPrim + l, fmaf(ak[l], hr, ak[TILE + l] * hi));
-                hrv[nmine] = hr;
-                hiv[nmine] = hi;
-            }
-            __syncthreads();
-            nmine = 0;
-            for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
-                const int k = e / TILE, l = e - k * TILE;
-                float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
-                ak[l] = hrv[nmine];
-                ak[TILE + l] = hiv[nmine];
-            }
-            __syncthreads();
+        const long long t = s_t;
+        if (t >= total) break;
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (s_first[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        if (threadIdx.x < TILE && in) {
-            const float gp = 0.5f * pv.y * sPrim[lane];
-            if (gp != 0.0f) atomicAdd(c.grad + pix, gp);
-        }
-        // phase 3: neighbour legs, warps split the neighbour rings
-        const int2 rr = g.ring_range[P.i];
-        for (int r = rr.x + warp; r <= rr.y; r += NWARPS)
-            adj_ring<M>(g, P, r, qg, pv.x, c.wdw, sA, sRow + (size_t)warp * ROW, c.grad, c.status);
-        __syncthreads();
+        bwd_tile<M>(items[lo].g, items[lo].c, (int)(t - s_first[lo]), smem);
     }
 }
 

@@ -31,13 +31,12 @@ __global__ void reduce_slots_kernel(const double* __restrict__ slots, int nslots
 
 // zeta_m(k1,k2) = S_m(k1,k2) / (scale * D(k1,k2)), Hermitian fill of the lower triangle,
 // zeta = 0 where D = 0.  With self-pair subtraction the diagonal loses
-// sum_i w_i d_i Q^k(i) (every m) and D loses sum_i w_i QW^k(i).
-__global__ void finalize_kernel(const double* __restrict__ sums, int K, int M, int self_subtract,
-                                double scale, double* zeta, double* norm, double* raw) {
+// sum_i w_i d_i Q^k(i) (every m) and D loses sum_i w_i QW^k(i).  One output entry
+// idx = (m, k1, k2) per call.
+__device__ __forceinline__ void finalize_one(const double* __restrict__ sums, int K, int M, int self_subtract,
+                                             double scale, double* zeta, double* norm, double* raw, int idx) {
     const int P = K * (K + 1) / 2;
     const int nS = (M + 1) * P;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (M + 1) * K * K) return;
     const int m = idx / (K * K);
     const int rem = idx - m * K * K;
     const int k1 = rem / K, k2 = rem - k1 * K;
@@ -66,11 +65,16 @@ __global__ void finalize_kernel(const double* __restrict__ sums, int K, int M, i
     if (m == 0) norm[rem] = d;
 }
 
-// H_m(k,k') = conj(C_m(k,k')) + C_m(k',k),  C = (dL/dRe zeta + i dL/dIm zeta) / D.
-__global__ void adjoint_prep_kernel(const double* __restrict__ dL, const double* __restrict__ norm, int K,
-                                    int M, float* H) {
+__global__ void finalize_kernel(const double* __restrict__ sums, int K, int M, int self_subtract,
+                                double scale, double* zeta, double* norm, double* raw) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (M + 1) * K * K) return;
+    finalize_one(sums, K, M, self_subtract, scale, zeta, norm, raw, idx);
+}
+
+// H_m(k,k') = conj(C_m(k,k')) + C_m(k',k),  C = (dL/dRe zeta + i dL/dIm zeta) / D.
+__device__ __forceinline__ void adjoint_prep_one(const double* __restrict__ dL, const double* __restrict__ norm,
+                                                 int K, float* H, int idx) {
     const int m = idx / (K * K);
     const int rem = idx - m * K * K;
     const int k = rem / K, kp = rem - k * K;
@@ -87,6 +91,62 @@ __global__ void adjoint_prep_kernel(const double* __restrict__ dL, const double*
     }
     H[2 * idx] = (float)(c1r + c2r);
     H[2 * idx + 1] = (float)(-c1i + c2i);
+}
+
+__global__ void adjoint_prep_kernel(const double* __restrict__ dL, const double* __restrict__ norm, int K,
+                                    int M, float* H) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (M + 1) * K * K) return;
+    adjoint_prep_one(dL, norm, K, H, idx);
+}
+
+// ------------------------------------------------------------------ batches
+// The batched forms run the same per-entry work for every plan of a batch at once:
+// blockIdx.y selects the plan, blockIdx.x strides over its entries.
+
+__global__ void batch_pack_kernel(const BatchIO* __restrict__ io) {
+    const BatchIO& b = io[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.npix;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float wi = b.w[i];
+        b.wdw[i] = make_float2(wi * b.delta[i], wi);
+    }
+}
+
+// Zeroes each plan's CTA slots and, when `with_grad`, its gradient.
+__global__ void batch_zero_kernel(const BatchIO* __restrict__ io, int with_grad) {
+    const BatchIO& b = io[blockIdx.y];
+    const int64_t ns = (int64_t)b.nslots * b.nent;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b.slots[i] = 0.0;
+    if (with_grad)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.npix;
+             i += (int64_t)gridDim.x * blockDim.x)
+            b.grad[i] = 0.0f;
+}
+
+__global__ void batch_reduce_kernel(const BatchIO* __restrict__ io) {
+    const BatchIO& b = io[blockIdx.y];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < b.nent; e += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int s = 0; s < b.nslots; ++s) acc += b.slots[(size_t)s * b.nent + e];
+        b.sums[e] = acc;
+    }
+}
+
+__global__ void batch_finalize_kernel(const BatchIO* __restrict__ io) {
+    const BatchIO& b = io[blockIdx.y];
+    const int nout = (b.M + 1) * b.K * b.K;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nout; idx += gridDim.x * blockDim.x)
+        finalize_one(b.sums, b.K, b.M, b.self_subtract, 1.0, b.zeta, b.norm, nullptr, idx);
+}
+
+__global__ void batch_adjoint_prep_kernel(const BatchIO* __restrict__ io) {
+    const BatchIO& b = io[blockIdx.y];
+    const int nout = (b.M + 1) * b.K * b.K;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nout; idx += gridDim.x * blockDim.x)
+        adjoint_prep_one(b.dL, b.norm, b.K, b.H, idx);
 }
 
 }  // namespace tpcf

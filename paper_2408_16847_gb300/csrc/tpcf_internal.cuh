@@ -57,6 +57,15 @@ struct MapCall {
     int self_subtract;      // subtract the j = k self term
 };
 
+// One plan of a batch (device-resident): its geometry, its per-call arguments and
+// the index of its first tile in the batch's concatenated work queue.
+constexpr int TPCF_MAX_BATCH = 256;
+struct BatchItem {
+    MapDev g;
+    MapCall c;
+    long long tile0;
+};
+
 // Entries of the per-tile partial sums: S for k1 <= k2 (complex), then D (k1 <= k2),
 // then, with self-pair subtraction, the two diagonals sum w d Q and sum w QW.
 inline __host__ __device__ int n_pairs_tri(int K) { return K * (K + 1) / 2; }

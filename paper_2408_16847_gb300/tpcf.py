@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import check, lib
+from ._capi import TpcfError, check, lib  # noqa: F401  (TpcfError re-exported)
 
 
 def _stream_ptr(stream: Optional[torch.cuda.Stream] = None) -> ctypes.c_void_p:
@@ -221,6 +221,10 @@ class Batch:
 
     def launch(self, stream=None) -> None:
         check(lib().tpcf_batch_launch(self._h, _stream_ptr(stream)), "tpcf_batch_launch")
+
+    def kernel_launches(self) -> int:
+        """Kernels in one replay of the batch's graph."""
+        return int(lib().tpcf_batch_kernel_launches(self._h))
 
     def close(self) -> None:
         if self._h is not None and self._h.value:

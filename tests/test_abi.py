@@ -58,4 +58,10 @@ def test_invalid_arguments_need_no_gpu(lib):
     assert lib.tpcf_backward(None, None, None, 0, 0, None, None, None, None) == 1
     assert lib.tpcf_plan_npoints(None) == -1
     lib.tpcf_plan_destroy(None)
+    assert lib.tpcf_batch_create(None, None, 1, None, None, None, None, None, None, None) == 1
+    hb = ctypes.c_void_p()
+    assert lib.tpcf_batch_create(ctypes.byref(hb), None, 0, None, None, None, None, None, None, None) == 1
+    assert lib.tpcf_batch_launch(None, None) == 1
+    assert lib.tpcf_batch_kernel_launches(None) == -1
+    lib.tpcf_batch_destroy(None)
     assert h.value is None
