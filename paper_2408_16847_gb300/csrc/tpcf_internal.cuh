@@ -43,6 +43,30 @@ struct MapDev {
     const double* E;            // [K+1] sin^2(theta_e / 2)
 };
 
+// Read-only device view of a catalogue plan: the points sorted into a sphere grid
+// of colatitude bands, each cut into equal longitude sectors (cells).  Points of a
+// cell are contiguous, cells are ordered band by band, sectors by longitude.
+constexpr int CAT_LUT = 512;  // entries of the bin lookup table (uniform in log2 chord^2)
+struct CatDev {
+    int64_t n;
+    int K, M;
+    const float4* p_hi;          // [n] sorted unit vectors, fp32 part (x, y, z, 0)
+    const float4* p_lo;          // [n] fp64 - fp32 remainders (x, y, z), w = sorted index bits
+    const double* xyz;           // [3n] sorted unit vectors, fp64
+    const int64_t* orig;         // [n] caller's index of each sorted point
+    const int64_t* cell_start;   // [ncells + 1] first sorted point of each cell
+    const int64_t* band_first;   // [nbands + 1] first cell of each band
+    const int64_t* band_ns;      // [nbands] sectors in each band
+    int nbands;
+    double hband;                // band height (rad)
+    double theta_max;            // outer bin edge (rad)
+    const float* E2;             // [K+1] chord^2 of the edges, fp32
+    const double* Ed2;           // [K+1] chord^2 of the edges, fp64
+    const unsigned char* lut;    // [CAT_LUT] bin at the lower end of each table cell
+    float lut_l0, lut_inv;       // table origin log2(E2[0]) and entries per unit of log2
+    int64_t ntiles;              // ceil(n / TILE)
+};
+
 // Per-call arguments of the map kernels.
 struct MapCall {
     const float2* wdw;      // [npix] (w * delta, w)

@@ -76,7 +76,8 @@ def test_batch_forward_matches_single_calls_and_oracle():
             zo = tpcf.as_complex(z1).cpu().numpy()
             assert np.isfinite(zb).all()
             assert np.abs(zb - zo).max() <= 1e-6 * max(np.abs(zo).max(), 1e-300), (replay, i)
-            np.testing.assert_allclose(ns[i].cpu().numpy(), n1.cpu().numpy(), rtol=1e-12, atol=0)
+            # D is summed in fp32 within a tile (shared-memory atomics, unordered)
+            np.testing.assert_allclose(ns[i].cpu().numpy(), n1.cpu().numpy(), rtol=1e-6, atol=0)
     for i, (nside, edges, M, sp) in enumerate(CASES):
         d, w = host[i]
         ref = oracle.zeta(oracle.pix2vec_ring(nside), d.astype(np.float64), w.astype(np.float64),
