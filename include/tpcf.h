@@ -91,14 +91,32 @@ const char* tpcf_last_error(void);
 tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const tpcf_bins* bins, void* stream);
 
 /*
- * Catalogue plan over n points given as unit vectors d_xyz (device, double[n][3]),
- * for point catalogues (the paper's estimator applies to any sample on the sphere,
- * section 3.1).  Sorts the points into a device-built sphere grid; the plan keeps
- * its own sorted copy, d_xyz may be freed after the call returns and the stream
- * has been synchronised.
+ * Catalogue plan over n points given as unit vectors d_xyz (device, double[n][3],
+ * used as given), for point catalogues: the estimator of section 3.1 applies to any
+ * sample on the sphere.  Sorts the points, on the device and on `stream`, into a
+ * sphere grid of colatitude bands cut into longitude sectors (about 32 points per
+ * cell on average); each pivot's neighbours are then read from the cells that the
+ * cap of radius theta_max around its tile of 32 pivots overlaps, and binned exactly
+ * (fp32 chord from hi/lo coordinates, FP64 decision within 2e-6 of an edge).  The
+ * plan keeps its own sorted copy: d_xyz may be freed once the call has returned.
+ * Forward calls take d_delta / d_w in the caller's point order, and pivot ranges are
+ * ranges of caller indices.  The adjoint and the pair count are map-only
+ * (TPCF_ERR_UNSUPPORTED).  1 <= n <= 2^31 - 1, else TPCF_ERR_INVALID_ARG.
  */
 tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_xyz, int64_t n,
                                      const tpcf_bins* bins, void* stream);
+
+/*
+ * zeta = d_sums / (scale * d_norm), per entry, 0 where the denominator is 0: the last
+ * step of an estimate whose sums and normalisation come from different runs.  The
+ * edge-corrected catalogue estimate (data with delta = 1, randoms with
+ * delta = -alpha, alpha = sum w_data / n_randoms) takes the raw sums S of the union
+ * and the norm D of a delta = 1 run over the randoms, with scale = alpha^3.
+ * d_sums and d_zeta use the zeta layout, d_norm the norm layout (device, caller
+ * owned).  Errors: INVALID_ARG for NULL, nbins / m_max out of range, scale not > 0.
+ */
+tpcf_status tpcf_normalize(const double* d_sums, const double* d_norm, double scale, int32_t nbins,
+                           int32_t m_max, double* d_zeta, void* stream);
 
 /* Number of points (pixels) of the plan; -1 if plan is NULL. */
 int64_t tpcf_plan_npoints(tpcf_plan plan);

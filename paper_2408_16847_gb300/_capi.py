@@ -22,7 +22,7 @@ MAX_M = 16
 # every exported entry point of include/tpcf.h
 EXPORTS = ["tpcf_status_string", "tpcf_last_error", "tpcf_plan_create_map", "tpcf_plan_create_catalog",
            "tpcf_plan_npoints", "tpcf_plan_kernel_launches", "tpcf_forward", "tpcf_forward_noalloc", "tpcf_backward", "tpcf_count_pairs", "tpcf_run_host", "tpcf_batch_create",
-           "tpcf_batch_launch", "tpcf_batch_kernel_launches", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync",
+           "tpcf_batch_launch", "tpcf_batch_kernel_launches", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync", "tpcf_normalize",
            "tpcf_plan_destroy"]
 
 
@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
     L.tpcf_batch_destroy.argtypes = [_vp]
     L.tpcf_forward_batched.restype = ctypes.c_int
     L.tpcf_forward_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32] + [ctypes.POINTER(_vp)] * 6 + [_vp]
+    L.tpcf_normalize.restype = ctypes.c_int
+    L.tpcf_normalize.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     L.tpcf_plan_sync.restype = ctypes.c_int
     L.tpcf_plan_sync.argtypes = [_vp]
     L.tpcf_plan_destroy.restype = None

@@ -29,6 +29,10 @@ TPCF_DECL_M(12) TPCF_DECL_M(13) TPCF_DECL_M(14) TPCF_DECL_M(15) TPCF_DECL_M(16)
 #undef TPCF_DECL_M
 cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi,
                              unsigned long long* counts, int grid, cudaStream_t s);
+// catalogue plans (catalog.cu)
+tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaStream_t s);
+tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
+                            double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s);
 
 struct MLaunch {
     cudaError_t (*fwd)(const MapDev&, const MapCall&, int, cudaStream_t);
@@ -224,13 +228,35 @@ extern "C" tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const
 
 extern "C" tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_xyz, int64_t n,
                                                 const tpcf_bins* bins, void* stream) {
-    (void)d_xyz;
-    (void)n;
-    (void)bins;
-    (void)stream;
     if (!out) return TPCF_ERR_INVALID_ARG;
     *out = nullptr;
-    return TPCF_ERR_UNSUPPORTED;
+    if (!d_xyz || n < 1 || n > 0x7fffffffLL) return TPCF_ERR_INVALID_ARG;
+    tpcf_status st = check_bins(bins);
+    if (st != TPCF_OK) return st;
+    tpcf_plan_s* P = new (std::nothrow) tpcf_plan_s();
+    if (!P) return TPCF_ERR_OOM;
+    P->kind = PLAN_CATALOG;
+    P->K = bins->nbins;
+    P->M = bins->m_max;
+    P->flags = bins->flags;
+    P->edges.assign(bins->theta_edges_rad, bins->theta_edges_rad + bins->nbins + 1);
+    P->npoints = n;
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "device query");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    st = build_catalog(P, d_xyz, n, s);
+    if (st != TPCF_OK) {
+        cudaStreamSynchronize(s);
+        delete P;
+        return st;
+    }
+    P->last_stream = s;
+    *out = P;
+    return TPCF_OK;
 }
 
 extern "C" int64_t tpcf_plan_npoints(tpcf_plan plan) { return plan ? plan->npoints : -1; }
@@ -277,6 +303,8 @@ extern "C" tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const 
     plan->last_stream = s;
     if (plan->kind == PLAN_MAP) return map_forward(plan, d_delta, d_w, pivot_begin, pivot_end, d_zeta, d_norm,
                                                    d_sums, s);
+    if (plan->kind == PLAN_CATALOG)
+        return catalog_forward(plan, d_delta, d_w, pivot_begin, pivot_end, d_zeta, d_norm, d_sums, s);
     return TPCF_ERR_UNSUPPORTED;
 }
 

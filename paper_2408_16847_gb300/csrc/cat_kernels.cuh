@@ -1,0 +1,290 @@
+// Catalogue forward kernel: the estimator of Sec. 3.1 (eqs. Xm.binned, zetamEst)
+// for points at arbitrary positions, found through the plan's sphere grid.
+//
+// A tile is 32 consecutive points of the grid order (spatially compact), one pivot
+// per lane.  Warp 0 bounds the tile's live pivots by a cap (centre, radius R); every
+// point within R + theta_max of the centre lies in the cells the cap overlaps, which
+// are a handful of contiguous index ranges per colatitude band.  The CTA's warps take
+// the bands round-robin, stage 32 candidates at a time in shared memory and let each
+// lane pair its pivot with all 32.  Per pair: the chord from fp32 hi/lo positions,
+// the bin from a log-scale lookup table (FP64 check within CAT_AMB of an edge), the
+// position angle from the pivot's local north/east basis, the harmonics by the
+// Chebyshev recurrences.  The per-lane register sums follow one bin at a time and
+// are added into the tile's shared-memory moments when the bin changes; the tile
+// contraction and the cross-CTA reduction are those of the map path.
+#pragma once
+
+#include "map_kernels.cuh"
+
+namespace tpcf {
+
+constexpr float CAT_AMB = 2.0e-6f;  // relative margin of fp32 chord^2 to an edge (error ~3e-7)
+constexpr double CAT_EPS = 1.0e-7;  // angular margin of the cell query (rad)
+
+// Bin of chord^2 c2 in fp64 over the edges (ties to the upper bin): -1 below the
+// first edge, K at or beyond the last.
+static __device__ __noinline__ int cat_exact_bin(const double* __restrict__ Ed2, int K, const double* __restrict__ xyz,
+                                          int64_t j, double px, double py, double pz) {
+    const double dx = xyz[3 * j] - px, dy = xyz[3 * j + 1] - py, dz = xyz[3 * j + 2] - pz;
+    const double c2 = dx * dx + dy * dy + dz * dz;
+    int k = -1;
+    while (k < K && c2 >= Ed2[k + 1]) ++k;
+    return k;
+}
+
+// fp32 bin of c2 from the lookup table, corrected against the fp32 edges.
+__device__ __forceinline__ int cat_bin(float c2, const float* sE2, const unsigned char* slut, float l0, float linv,
+                                       int K) {
+    const float x = (__log2f(c2) - l0) * linv;
+    int k = x < 0.0f ? -1 : (x >= (float)CAT_LUT ? K : (int)slut[(int)x]);
+    while (k < K && c2 >= sE2[k + 1]) ++k;
+    while (k >= 0 && c2 < sE2[k]) --k;
+    return k;
+}
+
+template <int M, bool SELF>
+__device__ __forceinline__ void cat_flush(float* sA, float* sW, float* sQ, float* sQW, int k, int lane,
+                                          float (&re)[M + 1], float (&im)[M + 1], float& W, float& Q, float& QW) {
+    float* a = sA + (size_t)k * (M + 1) * 2 * TILE;
+    atomicAdd(a + lane, re[0]);
+    re[0] = 0.0f;
+    im[0] = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= M; ++m) {
+        atomicAdd(a + (2 * m) * TILE + lane, re[m]);
+        atomicAdd(a + (2 * m + 1) * TILE + lane, im[m]);
+        re[m] = 0.0f;
+        im[m] = 0.0f;
+    }
+    atomicAdd(sW + k * TILE + lane, W);
+    W = 0.0f;
+    if (SELF) {
+        atomicAdd(sQ + k * TILE + lane, Q);
+        atomicAdd(sQW + k * TILE + lane, QW);
+        Q = 0.0f;
+        QW = 0.0f;
+    }
+}
+
+// Shared memory of the catalogue forward beyond the tile's moments: per-warp
+// staging of 32 candidates (hi, lo positions and (w d, w)).
+template <int M>
+__host__ __device__ inline size_t cat_tile_bytes(int K) {
+    return tile_floats<M>(K) * sizeof(float) + (size_t)NWARPS * TILE * (2 * sizeof(float4) + sizeof(float2));
+}
+
+template <int M, bool SELF>
+__global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall c) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_tile;
+    __shared__ double s_cap[4];  // centre (x, y, z), query radius
+    __shared__ float sE2[TPCF_MAX_BINS + 1];
+    __shared__ unsigned char slut[CAT_LUT];
+    const int K = g.K;
+    float* sA = smem;
+    float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
+    float* sQ = sW + K * TILE;
+    float* sQW = sQ + K * TILE;
+    float* sPiv = sQW + K * TILE;
+    float4* sCh = reinterpret_cast<float4*>(smem + tile_floats<M>(K));
+    float4* sCl = sCh + NWARPS * TILE;
+    float2* sCv = reinterpret_cast<float2*>(sCl + NWARPS * TILE);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t nfl = tile_floats<M>(K) - 2 * TILE;
+    for (int e = threadIdx.x; e <= K; e += NTHREADS) sE2[e] = g.E2[e];
+    for (int e = threadIdx.x; e < CAT_LUT; e += NTHREADS) slut[e] = g.lut[e];
+    double* slot = c.slots + (size_t)blockIdx.x * n_entries(K, M);
+    float4* wh = sCh + warp * TILE;
+    float4* wl = sCl + warp * TILE;
+    float2* wv = sCv + warp * TILE;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if ((long long)tile >= g.ntiles) break;
+        const int64_t si = (int64_t)tile * TILE + lane;
+        bool live = false;
+        float2 pv = make_float2(0.0f, 0.0f);
+        double px = 0.0, py = 0.0, pz = 1.0;
+        if (si < g.n) {
+            const int64_t o = g.orig[si];
+            if (o >= c.piv_lo && o < c.piv_hi) {
+                pv = c.wdw[si];
+                live = pv.y != 0.0f;
+                if (!live) pv = make_float2(0.0f, 0.0f);
+            }
+            px = g.xyz[3 * si];
+            py = g.xyz[3 * si + 1];
+            pz = g.xyz[3 * si + 2];
+        }
+        if (!__syncthreads_or(live)) continue;
+        for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
+        if (threadIdx.x < TILE) {
+            sPiv[lane] = pv.x;
+            sPiv[TILE + lane] = pv.y;
+        }
+        if (warp == 0) {
+            // bounding cap of the live pivots, in fp64
+            double sx = live ? px : 0.0, sy = live ? py : 0.0, sz = live ? pz : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            }
+            double nrm = sqrt(sx * sx + sy * sy + sz * sz);
+            if (!(nrm > 1e-300)) {  // live pivots cancel out: any centre will do (r is measured from it)
+                sx = 0.0;
+                sy = 0.0;
+                sz = 1.0;
+                nrm = 1.0;
+            }
+            const double cx = sx / nrm, cy = sy / nrm, cz = sz / nrm;
+            double r = 0.0;
+            if (live) {
+                const double dx = px - cx, dy = py - cy, dz = pz - cz;
+                const double ch = sqrt(dx * dx + dy * dy + dz * dz);
+                r = 2.0 * asin(fmin(1.0, 0.5 * ch));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+            if (lane == 0) {
+                s_cap[0] = cx;
+                s_cap[1] = cy;
+                s_cap[2] = cz;
+                s_cap[3] = r + g.theta_max + CAT_EPS;
+            }
+        }
+        __syncthreads();
+
+        // the lane's pivot: fp32 hi/lo position and local north / east basis
+        float hx = 0.0f, hy = 0.0f, hz = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
+        float nx, ny, nz, ex, ey;
+        {
+            hx = (float)px;
+            hy = (float)py;
+            hz = (float)pz;
+            lx = (float)(px - (double)hx);
+            ly = (float)(py - (double)hy);
+            lz = (float)(pz - (double)hz);
+            const double s2 = px * px + py * py;
+            if (s2 > 1e-24) {
+                const double is = 1.0 / sqrt(s2);
+                ex = (float)(-py * is);  // east = z x n / |z x n|
+                ey = (float)(px * is);
+                nx = (float)(-pz * px * is);  // north = n x east
+                ny = (float)(-pz * py * is);
+                nz = (float)(s2 * is);
+            } else {  // on the axis: any tangent basis of the same handedness
+                ex = 0.0f;
+                ey = 1.0f;
+                nx = (float)(-pz);
+                ny = 0.0f;
+                nz = 0.0f;
+            }
+        }
+
+        // cells within the query cap: band range and longitude half-width
+        const double cx = s_cap[0], cy = s_cap[1], cz = s_cap[2], Q = s_cap[3];
+        const double thc = atan2(sqrt(cx * cx + cy * cy), cz);
+        double phc = atan2(cy, cx);
+        if (phc < 0.0) phc += 2.0 * M_PI;
+        int b0 = 0, b1 = g.nbands - 1;
+        bool full = true;
+        double dphi = M_PI;
+        if (Q < M_PI) {
+            b0 = max(0, (int)floor((thc - Q) / g.hband));
+            b1 = min(g.nbands - 1, (int)floor((thc + Q) / g.hband));
+            const double sq = sin(Q), st = sin(thc);
+            if (thc - Q > 0.0 && thc + Q < M_PI && sq < st) {
+                full = false;
+                dphi = asin(sq / st) + CAT_EPS;
+            }
+        }
+
+        float re[M + 1], im[M + 1];
+#pragma unroll
+        for (int m = 0; m <= M; ++m) {
+            re[m] = 0.0f;
+            im[m] = 0.0f;
+        }
+        float W = 0.0f, Qs = 0.0f, QW = 0.0f;
+        int kcur = -1;
+        for (int b = b0 + warp; b <= b1; b += NWARPS) {
+            const int64_t ns = g.band_ns[b];
+            const int64_t cf = g.band_first[b];
+            // at most two cell ranges (the sector range may wrap around phi = 0)
+            int64_t ca0 = cf, ca1 = cf + ns, cb0 = 0, cb1 = 0;
+            if (!full) {
+                const double scale = (double)ns / (2.0 * M_PI);
+                const int64_t sa = (int64_t)floor((phc - dphi) * scale);
+                const int64_t sb = (int64_t)floor((phc + dphi) * scale);
+                const int64_t len = sb - sa + 1;
+                if (len < ns) {
+                    int64_t s0 = sa % ns;
+                    if (s0 < 0) s0 += ns;
+                    ca0 = cf + s0;
+                    if (s0 + len <= ns) {
+                        ca1 = cf + s0 + len;
+                    } else {
+                        ca1 = cf + ns;
+                        cb0 = cf;
+                        cb1 = cf + (s0 + len - ns);
+                    }
+                }
+            }
+#pragma unroll 1
+            for (int sg = 0; sg < 2; ++sg) {
+                const int64_t cl0 = sg == 0 ? ca0 : cb0, cl1 = sg == 0 ? ca1 : cb1;
+                if (cl1 <= cl0) continue;
+                const int64_t p0 = g.cell_start[cl0], p1 = g.cell_start[cl1];
+                for (int64_t base = p0; base < p1; base += TILE) {
+                    const int64_t j = base + lane;
+                    __syncwarp();
+                    if (j < p1) {
+                        wh[lane] = g.p_hi[j];
+                        wl[lane] = g.p_lo[j];
+                        wv[lane] = c.wdw[j];
+                    }
+                    __syncwarp();
+                    const int cnt = (int)min((int64_t)TILE, p1 - base);
+                    for (int u = 0; u < cnt; ++u) {
+                        const float4 qh = wh[u], ql = wl[u];
+                        const float2 v = wv[u];
+                        const float dx = (qh.x - hx) + (ql.x - lx);
+                        const float dy = (qh.y - hy) + (ql.y - ly);
+                        const float dz = (qh.z - hz) + (ql.z - lz);
+                        const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
+                        const int e1 = max(k, 0), e2 = min(k + 1, K);
+                        if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
+                            k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), px, py, pz);
+                        const bool on = k >= 0 && k < K;
+                        if (on && k != kcur) {
+                            if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, re, im, W, Qs, QW);
+                            kcur = k;
+                        }
+                        const float N = fmaf(dx, nx, fmaf(dy, ny, dz * nz));
+                        const float E = fmaf(dx, ex, dy * ey);
+                        const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                        const float wd = on ? v.x : 0.0f;
+                        const float ww = on ? v.y : 0.0f;
+                        harmonics<M>(re, im, N * rinv, E * rinv, wd, wd);
+                        W += ww;
+                        if (SELF) {
+                            Qs = fmaf(wd, wd, Qs);
+                            QW = fmaf(ww, ww, QW);
+                        }
+                    }
+                }
+            }
+        }
+        if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, re, im, W, Qs, QW);
+        __syncthreads();
+        tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+        __syncthreads();
+    }
+}
+
+}  // namespace tpcf

@@ -1,6 +1,6 @@
 // Per-M instantiation of the map kernels.  The build compiles this file once for
 // every multipole limit TPCF_M = 0..TPCF_MAX_M and links the objects together.
-#include "map_kernels.cuh"
+#include "cat_kernels.cuh"
 
 #ifndef TPCF_M
 #error "compile with -DTPCF_M=<m_max>"
@@ -121,6 +121,36 @@ int TPCF_CAT(batch_bwd_occupancy_m, TPCF_M)(size_t smem) {
     int nb = 0;
     cudaFuncSetAttribute(batch_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_bwd_kernel<TPCF_M>, NTHREADS, smem);
+    return nb;
+}
+
+// Catalogue forward.
+cudaError_t TPCF_CAT(cat_fwd_launch_m, TPCF_M)(const CatDev& g, const MapCall& c, int grid, cudaStream_t s) {
+    const size_t smem = cat_tile_bytes<TPCF_M>(g.K);
+    if (c.self_subtract) {
+        auto* k = cat_fwd_kernel<TPCF_M, true>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    } else {
+        auto* k = cat_fwd_kernel<TPCF_M, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    }
+    return cudaGetLastError();
+}
+
+int TPCF_CAT(cat_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
+    const size_t smem = cat_tile_bytes<TPCF_M>(K);
+    int nb = 0;
+    if (self_subtract) {
+        cudaFuncSetAttribute(cat_fwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cat_fwd_kernel<TPCF_M, true>, NTHREADS, smem);
+    } else {
+        cudaFuncSetAttribute(cat_fwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cat_fwd_kernel<TPCF_M, false>, NTHREADS, smem);
+    }
     return nb;
 }
 

@@ -34,6 +34,7 @@ struct tpcf_plan_s {
     std::vector<double> edges;
     std::vector<void*> allocs;  // everything freed by destroy
     MapDev map{};
+    tpcf::CatDev cat{};
     // per-call scratch
     float2* wdw = nullptr;
     double* slots = nullptr;

@@ -183,6 +183,17 @@ def as_complex(zeta: torch.Tensor) -> torch.Tensor:
     return torch.view_as_complex(zeta)
 
 
+def normalize(sums: torch.Tensor, norm: torch.Tensor, scale: float = 1.0, stream=None) -> torch.Tensor:
+    """zeta = sums / (scale * norm) on the device (tpcf_normalize); sums (M+1,K,K,2)."""
+    M1, K = sums.shape[0], sums.shape[1]
+    _need(sums, torch.float64, M1 * K * K * 2, "sums")
+    _need(norm, torch.float64, K * K, "norm")
+    zeta = torch.empty_like(sums)
+    check(lib().tpcf_normalize(_ptr(sums), _ptr(norm), float(scale), K, M1 - 1, _ptr(zeta), _stream_ptr(stream)),
+          "tpcf_normalize")
+    return zeta
+
+
 class ZetaFn(torch.autograd.Function):
     """zeta = ZetaFn.apply(delta, w, plan[, lo, hi]) with a hand-written adjoint.
 
