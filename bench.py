@@ -1,14 +1,25 @@
 #!/usr/bin/env python
 """Throughput of the harmonic 3PCF estimator on GB300: neighbour pairs/s.
 
-One step = one pass of the whole estimator over one full-sky map: the forward
-(geometry tables are plan state; neighbour search, binning, harmonics, contraction,
-normalisation) and the adjoint dL/d(delta) of L = sum c Re zeta.  Default workload:
-HEALPix Nside 4096 (201,326,592 pixels), 20 log bins over 0.1-2 deg, m <= 10.
+One step = one pass of the whole estimator over one batch of synthetic input:
+
+  fullsky_nside4096 (default)  forward (neighbour search, binning, harmonics,
+                               contraction, normalisation) + adjoint dL/d(delta) of
+                               L = sum c Re zeta, HEALPix Nside 4096 (201,326,592
+                               pixels), 20 log bins 0.1-2 deg, m <= 10
+  masked_map_nside1024,
+  fullsky_nside512, map_nside64  the same pass on smaller maps (fullsky_nside512 is
+                               the case profiled with ncu)
+  catalog_2e7                  catalogue D-R estimate: forward over 2e7 clustered
+                               points + 6e7 randoms, forward over the randoms,
+                               normalisation (16 lin bins 0.1-2 deg, m <= 10)
+  batched_maps                 64 maps of mixed Nside / bins / m_max, forward +
+                               adjoint in one graph-captured launch sequence
+                               (--batch-nsides scales the Nside set down)
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl gb300|reference]
 
-Under torchrun each rank runs an independent map of the same size on its own GPU
+Under torchrun each rank runs an independent input of the same size on its own GPU
 (weak scaling, no data-path collective); rank 0 prints ONE JSON line.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 """
@@ -31,6 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+MAP_WORKLOADS = ("fullsky_nside4096", "masked_map_nside1024", "fullsky_nside512", "map_nside64")
 
 
 def log(*a):
@@ -39,11 +51,9 @@ def log(*a):
 
 # ---------------------------------------------------------------- workloads
 
-def workload(name):
+def map_workload(name):
     import synth
-    table = {"fullsky_nside4096": synth.fullsky_nside4096, "masked_map_nside1024": synth.masked_map_nside1024,
-             "map_nside64": synth.map_nside64}
-    return table[name]()
+    return getattr(synth, name)()
 
 
 def map_inputs(wl, rank: int):
@@ -65,13 +75,33 @@ def map_inputs(wl, rank: int):
     return np.ascontiguousarray(d, np.float32), wl.weights().astype(np.float32)
 
 
+def catalog_inputs(rank: int):
+    """Union (data then randoms) positions, delta, w; randoms positions; alpha."""
+    import synth
+    wl = synth.catalog_2e7()
+    xd, wd = wl.data()
+    xr = wl.randoms()
+    if rank > 0:  # an independent draw per rank
+        g = synth.rng(wl.seed + 9000 + rank)
+        xd = synth.clustered_catalog(wl.n_points, wl.n_parents, wl.offset_sigma_deg, wl.seed + 9100 + rank)
+        xr = synth.uniform_sphere(wl.n_randoms, g)
+    wd32 = wd.astype(np.float32)
+    alpha = float(wd32.astype(np.float64).sum()) / len(xr)
+    nd, nr = len(xd), len(xr)
+    xu = np.concatenate([xd, xr])
+    du = np.concatenate([np.ones(nd, np.float32), np.full(nr, -alpha, np.float32)])
+    wu = np.concatenate([wd32, np.ones(nr, np.float32)])
+    return wl, xu, du, wu, xr, float(np.float32(alpha))
+
+
 # ------------------------------------------------------------- roofline model
 
 def flops_per_pair(M: int, adjoint: bool):
-    """FP32 flops (FMA = 2) of the implemented per-pair arithmetic, for a pixel visited
-    singly and for one visited as half of a mirror pair.  Counted from the pixel loop:
-    position angle 29 (series for sin/cos of half the longitude offset, east/north
-    components, normalisation), harmonics 2 recurrences + 2 accumulations per m >= 2."""
+    """FP32 flops (FMA = 2) of the implemented per-pair arithmetic of the map kernels,
+    for a pixel visited singly and for one visited as half of a mirror pair.  Counted
+    from the pixel loop: position angle 29 (series for sin/cos of half the longitude
+    offset, east/north components, normalisation), harmonics 2 recurrences + 2
+    accumulations per m >= 2."""
     mm = max(M - 1, 0)
     if not adjoint:
         single = 29 + 1 + 1 + 2 + 2 + 1 + 6 * mm + 1          # ~ 37 + 6 (M - 1)
@@ -80,6 +110,17 @@ def flops_per_pair(M: int, adjoint: bool):
         single = 29 + 2 + 1 + 1 + 8 * mm + 3
         mirror = (29 + 2 + 1 + 1 + 8 * mm + 6) / 2.0
     return single, mirror
+
+
+def cat_flops_per_pair(M: int):
+    """FP32 flops of the catalogue pair loop: chord from hi/lo differences 11, bin
+    lookup 4, north/east components and normalisation 14, harmonics 6 per m >= 2
+    plus 6 for m <= 1."""
+    return 35 + 6 * max(M - 1, 0)
+
+
+def fp32_peak_tflops(clk):
+    return SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
 
 
 # --------------------------------------------------------------- GPU clocks
@@ -131,13 +172,12 @@ class ClockSampler:
 # -------------------------------------------------------------- CPU baseline
 
 def oracle_sample(wl, d32, w32, n_piv: int):
-    """The FP64 oracle, as it stands, on a bounded sample: n_piv consecutive pivots on
-    the belt ring at z = 1/2 (outside the galactic mask), neighbours from every pixel
-    within the outer bin edge.
+    """The FP64 oracle, as it stands, on a bounded sample of a map workload: n_piv
+    consecutive pivots on the belt ring at z = 1/2 (outside the galactic mask),
+    neighbours from every pixel within the outer bin edge.
     Returns timings, pair count, the pivot range and the oracle's zeta (for parity)."""
     import oracle
     nside = wl.nside
-    npix = 12 * nside * nside
     ring = (5 * nside) // 4  # z = 1/2 (1-based ring number)
     first = 2 * nside * (nside - 1) + 4 * nside * (ring - nside)
     lo, hi = first, first + n_piv
@@ -153,7 +193,7 @@ def oracle_sample(wl, d32, w32, n_piv: int):
     d = d32[a:b].astype(np.float64)
     w = w32[a:b].astype(np.float64)
     piv = np.arange(lo - a, hi - a)
-    K, M = wl.bins.nbins, wl.bins.m_max
+    M = wl.bins.m_max
     cot = wl.cotangent()
     t0 = time.perf_counter()
     ref = oracle.zeta(xyz, d, w, wl.bins.edges_deg, M, pivots=piv)
@@ -161,10 +201,222 @@ def oracle_sample(wl, d32, w32, n_piv: int):
     oracle.gradient(xyz, d, w, wl.bins.edges_deg, M, cot.astype(np.complex128), pivots=piv, targets=piv)
     t2 = time.perf_counter()
     return dict(t_fwd=t1 - t0, t_bwd=t2 - t1, pairs=ref["pairs"], lo=lo, hi=hi, zeta=ref["zeta"],
-                cores=int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), npts=len(idx))
+                cores=int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), npts=len(idx),
+                desc="%d pivots at z=0.5 of %s (neighbours from %d pixels)" % (n_piv, wl.name, len(idx)))
+
+
+def oracle_sample_catalog(xu, du, wu, edges, M, n_piv: int):
+    """The oracle's forward on n_piv union pivots (half data, half randoms) with
+    neighbours from every point.  Returns timing, pairs, the pivot index range
+    (data part) and the oracle's raw sums for those pivots."""
+    import oracle
+    nd = int(np.sum(du > 0))
+    lo, hi = 1_000_000, 1_000_000 + n_piv
+    t0 = time.perf_counter()
+    ref = oracle.zeta(xu, du.astype(np.float64), wu.astype(np.float64), edges, M, pivots=np.arange(lo, hi))
+    t1 = time.perf_counter()
+    assert hi <= nd
+    return dict(t_fwd=t1 - t0, t_bwd=0.0, pairs=ref["pairs"], lo=lo, hi=hi, S=ref["S"],
+                cores=int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), npts=len(xu),
+                desc="%d data pivots of catalog_2e7 (neighbours from all %d points), FP64 forward" %
+                     (n_piv, len(xu)))
 
 
 # ---------------------------------------------------------------- GPU arm
+
+def setup_map(args, dev, rank):
+    import torch
+    from paper_2408_16847_gb300 import tpcf
+
+    wl = map_workload(args.workload)
+    t0 = time.time()
+    d32, w32 = map_inputs(wl, rank)
+    log("[rank %d] inputs ready in %.1fs" % (rank, time.time() - t0))
+    K, M = wl.bins.nbins, wl.bins.m_max
+    plan = tpcf.Plan.map(wl.nside, wl.bins.edges_deg, M, contract=args.contract)
+    d_dev = torch.from_numpy(d32).to(dev)
+    w_dev = torch.from_numpy(w32).to(dev)
+    cot = wl.cotangent()
+    g_dev = torch.zeros((M + 1, K, K, 2), dtype=torch.float64, device=dev)
+    g_dev[..., 0] = torch.from_numpy(cot).to(dev)
+    total, n_sym, n_single = plan.count_pairs(w_dev)
+    state = {}
+
+    def step(ev=None):
+        zeta, norm = plan.forward(d_dev, w_dev)
+        if ev is not None:
+            ev.record(torch.cuda.current_stream())
+        state["grad"] = plan.backward(d_dev, w_dev, norm, g_dev)
+
+    # e2e: the public host-buffer call, with its copies inside the timed region
+    h_d = torch.from_numpy(d32).pin_memory()
+    h_w = torch.from_numpy(w32).pin_memory()
+    h_dl = torch.from_numpy(np.stack([cot, np.zeros_like(cot)], axis=-1).copy()).pin_memory()
+    h_z = torch.empty((M + 1, K, K, 2), dtype=torch.float64).pin_memory()
+    h_n = torch.empty((K, K), dtype=torch.float64).pin_memory()
+    h_g = torch.empty(plan.npoints, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        plan.run_host_into(h_d, h_w, h_dl, out=(h_z, h_n, h_g))
+
+    f_single, f_mirror = flops_per_pair(M, adjoint=False)
+    a_single, a_mirror = flops_per_pair(M, adjoint=True)
+    fwd_flops = n_single * f_single + n_sym * f_mirror
+    adj_flops = n_single * a_single + n_sym * a_mirror
+
+    def cpu_baseline(n_piv):
+        s = oracle_sample(wl, d32, w32, n_piv)
+        zs, _ = plan.forward(d_dev, w_dev, (s["lo"], s["hi"]))
+        zg = tpcf.as_complex(zs).cpu().numpy()
+        zo = s["zeta"]
+        per_m = [float(np.abs(zg[m] - zo[m]).max() / max(np.abs(zo[m]).max(), 1e-300)) for m in range(M + 1)]
+        glob = float(np.abs(zg - zo).max() / np.abs(zo).max())
+        return s, {"pivots": s["hi"] - s["lo"], "max_rel_err_per_m": max(per_m),
+                   "max_rel_err_vs_max_zeta": glob, "tolerance": 1e-5}
+
+    config = {"workload": wl.name, "nside": wl.nside, "npix": 12 * wl.nside * wl.nside,
+              "bins": "%d %s bins %.2f-%.2f deg" % (K, "lin" if wl.name == "map_nside64" else "log",
+                                                    wl.bins.edges_deg[0], wl.bins.edges_deg[-1]),
+              "m_max": M, "pass": "forward + adjoint", "pairs_per_step_per_gpu": total,
+              "contraction": "tensor cores, TF32x3" if args.contract == "tc" else "FP32 pipe",
+              "l2": "inputs larger than L2 (%.2f GB of (w d, w) per map)" % (8 * 12 * wl.nside ** 2 / 1e9)
+              if 12 * wl.nside ** 2 * 8 > 129e6 else "L2 flushed between steps",
+              "parallelism": "independent map per GPU"}
+    return dict(step=step, split=("forward", "adjoint"), pairs=total, e2e=e2e_step,
+                e2e_bytes=(h_d.numel() * 4 + h_w.numel() * 4 + h_dl.numel() * 8,
+                           h_z.numel() * 8 + h_n.numel() * 8 + h_g.numel() * 4),
+                launches=plan.kernel_launches, config=config, cpu_baseline=cpu_baseline,
+                roofline=lambda t1, t2, clk: {
+                    "bound": "alu", "kernel": "map_bwd_kernel",
+                    "achieved": (fwd_flops + adj_flops) / (t2 * 1e-3) / 1e12,  # adjoint recomputes the forward
+                    "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s",
+                    "forward_kernel_tflops": fwd_flops / (t1 * 1e-3) / 1e12},
+                small_l2=12 * wl.nside ** 2 * 8 <= 129e6, close=plan.close)
+
+
+def setup_catalog(args, dev, rank):
+    import torch
+    from paper_2408_16847_gb300 import tpcf
+
+    t0 = time.time()
+    wl, xu, du, wu, xr, alpha32 = catalog_inputs(rank)
+    log("[rank %d] catalogue ready in %.1fs (%d + %d points)" % (rank, time.time() - t0, len(xu) - len(xr), len(xr)))
+    K, M = wl.bins.nbins, wl.bins.m_max
+    edges = wl.bins.edges_deg
+    xu_dev = torch.from_numpy(xu).to(dev)
+    pu = tpcf.Plan.catalog(xu_dev, edges, M)
+    del xu_dev
+    xr_dev = torch.from_numpy(np.ascontiguousarray(xr)).to(dev)
+    pr = tpcf.Plan.catalog(xr_dev, edges, M)
+    del xr_dev
+    nr = len(xr)
+    du_dev = torch.from_numpy(du).to(dev)
+    wu_dev = torch.from_numpy(wu).to(dev)
+    one_dev = torch.ones(nr, dtype=torch.float32, device=dev)
+    cu, _, _ = pu.count_pairs(wu_dev)
+    cr, _, _ = pr.count_pairs(one_dev)
+    scale = alpha32 ** 3
+    state = {}
+
+    def step(ev=None):
+        _, _, S = pu.forward(du_dev, wu_dev, want_sums=True)
+        if ev is not None:
+            ev.record(torch.cuda.current_stream())
+        _, DR = pr.forward(one_dev, one_dev)
+        state["zeta"] = tpcf.normalize(S, DR, scale)
+
+    h_du = torch.from_numpy(du).pin_memory()
+    h_wu = torch.from_numpy(wu).pin_memory()
+    h_one = torch.ones(nr, dtype=torch.float32).pin_memory()
+    h_z = torch.empty((M + 1, K, K, 2), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        d = h_du.to(dev, non_blocking=True)
+        w = h_wu.to(dev, non_blocking=True)
+        o = h_one.to(dev, non_blocking=True)
+        _, _, S = pu.forward(d, w, want_sums=True)
+        _, DR = pr.forward(o, o)
+        h_z.copy_(tpcf.normalize(S, DR, scale), non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    flops = (cu + cr) * cat_flops_per_pair(M)
+
+    def cpu_baseline(n_piv):
+        s = oracle_sample_catalog(xu, du, wu, edges, M, n_piv)
+        _, _, S = pu.forward(du_dev, wu_dev, (s["lo"], s["hi"]), want_sums=True)
+        sg = tpcf.as_complex(S).cpu().numpy()
+        so = s["S"]
+        per_m = [float(np.abs(sg[m] - so[m]).max() / max(np.abs(so[m]).max(), 1e-300)) for m in range(M + 1)]
+        return s, {"pivots": s["hi"] - s["lo"], "quantity": "raw sums S", "max_rel_err_per_m": max(per_m),
+                   "tolerance": 1e-5}
+
+    config = {"workload": wl.name, "points": len(xu) - nr, "randoms": nr,
+              "bins": "%d lin bins %.2f-%.2f deg" % (K, edges[0], edges[-1]), "m_max": M,
+              "pass": "D-R forward (union) + randoms forward + normalisation",
+              "pairs_per_step_per_gpu": cu + cr, "pairs_union": cu, "pairs_randoms": cr,
+              "l2": "inputs larger than L2", "parallelism": "independent catalogue per GPU"}
+    return dict(step=step, split=("union_forward", "randoms_forward"), pairs=cu + cr, e2e=e2e_step,
+                e2e_bytes=(h_du.numel() * 4 + h_wu.numel() * 4 + h_one.numel() * 4, h_z.numel() * 8),
+                launches=lambda: pu.kernel_launches() + pr.kernel_launches(), extra_launches_per_step=1,
+                config=config,
+                cpu_baseline=cpu_baseline,
+                roofline=lambda t1, t2, clk: {
+                    "bound": "alu", "kernel": "cat_fwd_kernel",
+                    "achieved": flops / ((t1 + t2) * 1e-3) / 1e12, "peak": fp32_peak_tflops(clk),
+                    "unit": "TFLOP/s"},
+                small_l2=False, close=lambda: (pu.close(), pr.close()))
+
+
+def setup_batch(args, dev, rank):
+    import torch
+    import synth
+    from paper_2408_16847_gb300 import tpcf
+
+    nsides = tuple(int(x) for x in args.batch_nsides.split(","))
+    wls = synth.batched_maps(64, nsides)
+    plans, ds, ws, zs, ns, dls, gs = [], [], [], [], [], [], []
+    total = 0
+    flops = 0.0
+    for wl in wls:
+        K, M = wl.bins.nbins, wl.bins.m_max
+        d32, w32 = map_inputs(wl, rank)
+        p = tpcf.Plan.map(wl.nside, wl.bins.edges_deg, M)
+        plans.append(p)
+        ds.append(torch.from_numpy(d32).to(dev))
+        ws.append(torch.from_numpy(w32).to(dev))
+        zs.append(torch.empty((M + 1, K, K, 2), dtype=torch.float64, device=dev))
+        ns.append(torch.empty((K, K), dtype=torch.float64, device=dev))
+        g = torch.zeros((M + 1, K, K, 2), dtype=torch.float64, device=dev)
+        g[..., 0] = torch.from_numpy(wl.cotangent()).to(dev)
+        dls.append(g)
+        gs.append(torch.empty(12 * wl.nside ** 2, dtype=torch.float32, device=dev))
+        t, sym, single = p.count_pairs(ws[-1])
+        total += t
+        fs, fm = flops_per_pair(M, False)
+        as_, am = flops_per_pair(M, True)
+        flops += single * (fs + as_) + sym * (fm + am)
+    batch = tpcf.Batch(plans, ds, ws, zs, ns, dls, gs)
+
+    def step(ev=None):
+        batch.launch()
+        if ev is not None:
+            ev.record(torch.cuda.current_stream())
+
+    config = {"workload": "batched_maps", "maps": len(wls), "nsides": list(nsides),
+              "bins": "8-24 lin/log bins over 0.2-4 deg", "m_max": "6-12",
+              "pass": "forward + adjoint, one graph replay", "pairs_per_step_per_gpu": total,
+              "kernels_per_replay": batch.kernel_launches(),
+              "l2": "inputs larger than L2" if sum(12 * n * n for n in (wl.nside for wl in wls)) * 8 > 129e6
+              else "L2-resident inputs", "parallelism": "independent batch per GPU"}
+    if nsides != (256, 512, 1024, 2048):
+        config["scaled"] = "Nside set scaled down from 256/512/1024/2048"
+    return dict(step=step, split=("batch", None), pairs=total, e2e=None, e2e_bytes=(0, 0),
+                launches=plans[0].kernel_launches, config=config, cpu_baseline=None,
+                roofline=lambda t1, t2, clk: {"bound": "alu", "kernel": "batch_bwd_kernel",
+                                              "achieved": flops / (t1 * 1e-3) / 1e12,
+                                              "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s"},
+                small_l2=False, close=lambda: (batch.close(), [p.close() for p in plans]))
+
 
 def run_gpu(args):
     import torch
@@ -183,29 +435,20 @@ def run_gpu(args):
         build()
     if world > 1:
         dist.barrier()
-    from paper_2408_16847_gb300 import tpcf
 
-    wl = workload(args.workload)
-    t0 = time.time()
-    d32, w32 = map_inputs(wl, rank)
-    log("[rank %d] inputs ready in %.1fs" % (rank, time.time() - t0))
-    K, M = wl.bins.nbins, wl.bins.m_max
-    plan = tpcf.Plan.map(wl.nside, wl.bins.edges_deg, M)
-    d_dev = torch.from_numpy(d32).to(dev)
-    w_dev = torch.from_numpy(w32).to(dev)
-    cot = wl.cotangent()
-    g_dev = torch.zeros((M + 1, K, K, 2), dtype=torch.float64, device=dev)
-    g_dev[..., 0] = torch.from_numpy(cot).to(dev)
-    total, n_sym, n_single = plan.count_pairs(w_dev)
+    if args.workload in MAP_WORKLOADS:
+        W = setup_map(args, dev, rank)
+    elif args.workload == "catalog_2e7":
+        W = setup_catalog(args, dev, rank)
+    elif args.workload == "batched_maps":
+        W = setup_batch(args, dev, rank)
+    else:
+        raise SystemExit("unknown workload " + args.workload)
     stream = torch.cuda.current_stream()
-
-    def step():
-        zeta, norm = plan.forward(d_dev, w_dev)
-        grad = plan.backward(d_dev, w_dev, norm, g_dev)
-        return zeta, grad
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if W["small_l2"] else None
 
     for _ in range(args.warmup):
-        step()
+        W["step"]()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -216,87 +459,70 @@ def run_gpu(args):
     except Exception:
         pass
     clocks = ClockSampler(gpu_id)
-    launches0 = plan.kernel_launches()
+    launches0 = W["launches"]()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
     for k in range(args.steps):
+        if flush is not None:
+            flush.fill_(float(k))  # write a buffer larger than L2 between steps
         ev[k][0].record(stream)
-        zeta, norm = plan.forward(d_dev, w_dev)
-        ev[k][1].record(stream)
-        grad = plan.backward(d_dev, w_dev, norm, g_dev)
+        W["step"](ev[k][1])
         ev[k][2].record(stream)
-    end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    launches = plan.kernel_launches() - launches0
-    total_ms = start.elapsed_time(end)
-    t_fwd = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
-    t_bwd = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
-    plan.sync()
-    t_max = torch.tensor([total_ms, sum(t_fwd), sum(t_bwd)], dtype=torch.float64, device=dev)
+    launches = W["launches"]() - launches0 + W.get("extra_launches_per_step", 0) * args.steps
+    t1 = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t2 = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    total_ms = sum(ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps))
+    t_max = torch.tensor([total_ms, sum(t1), sum(t2)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms, fwd_ms, bwd_ms = (float(v) for v in t_max.cpu())
+    total_ms, ms1, ms2 = (float(v) for v in t_max.cpu())
     ms_step = total_ms / args.steps
-    value = world * total * args.steps / (total_ms * 1e-3)
+    value = world * W["pairs"] * args.steps / (total_ms * 1e-3)
 
-    # e2e: the public host-buffer call, with its copies inside the timed region
-    h_d = torch.from_numpy(d32).pin_memory()
-    h_w = torch.from_numpy(w32).pin_memory()
-    h_dl = torch.from_numpy(np.stack([cot, np.zeros_like(cot)], axis=-1).copy()).pin_memory()
-    h_z = torch.empty((M + 1, K, K, 2), dtype=torch.float64).pin_memory()
-    h_n = torch.empty((K, K), dtype=torch.float64).pin_memory()
-    h_g = torch.empty(plan.npoints, dtype=torch.float32).pin_memory()
-    plan.run_host_into(h_d, h_w, h_dl, out=(h_z, h_n, h_g))
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    e_start = torch.cuda.Event(enable_timing=True)
-    e_end = torch.cuda.Event(enable_timing=True)
-    e_start.record(stream)
-    for _ in range(args.steps):
-        plan.run_host_into(h_d, h_w, h_dl, out=(h_z, h_n, h_g))
-    e_end.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = torch.tensor([e_start.elapsed_time(e_end), (time.perf_counter() - t0) * 1e3], dtype=torch.float64,
-                          device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_ms.max().cpu())
-    e2e_value = world * total * args.steps / (e2e_ms * 1e-3)
-    h2d = h_d.numel() * 4 + h_w.numel() * 4 + h_dl.numel() * 8
-    d2h = h_z.numel() * 8 + h_n.numel() * 8 + h_g.numel() * 4
+    e2e = None
+    if W["e2e"] is not None and args.e2e:
+        W["e2e"]()  # first call allocates the staging buffers
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
+        e_start.record(stream)
+        for _ in range(args.steps):
+            W["e2e"]()
+        e_end.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = torch.tensor([e_start.elapsed_time(e_end), (time.perf_counter() - t0) * 1e3],
+                              dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+        e2e_ms = float(e2e_ms.max().cpu())
+        e2e = {"value": world * W["pairs"] * args.steps / (e2e_ms * 1e-3), "unit": "pairs/s",
+               "h2d_bytes_per_step": W["e2e_bytes"][0], "d2h_bytes_per_step": W["e2e_bytes"][1]}
 
     result = None
     if rank == 0:
-        f_single, f_mirror = flops_per_pair(M, adjoint=False)
-        a_single, a_mirror = flops_per_pair(M, adjoint=True)
-        fwd_flops = n_single * f_single + n_sym * f_mirror
-        adj_flops = n_single * a_single + n_sym * a_mirror
-        bwd_s = bwd_ms * 1e-3 / args.steps
-        fwd_s = fwd_ms * 1e-3 / args.steps
-        peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
-        achieved = (fwd_flops + adj_flops) / bwd_s / 1e12  # adjoint kernel recomputes the forward
+        roof = W["roofline"](ms1 / args.steps, ms2 / args.steps, clk)
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
         cpu = None
         parity = None
-        if world == 1 and args.cpu_baseline:
+        if world == 1 and args.cpu_baseline and W["cpu_baseline"] is not None:
             log("[rank 0] CPU oracle sample ...")
-            s = oracle_sample(wl, d32, w32, args.cpu_pivots)
+            s, parity = W["cpu_baseline"](args.cpu_pivots)
             cpu = {"value": s["pairs"] / (s["t_fwd"] + s["t_bwd"]), "unit": "pairs/s", "cores": s["cores"],
                    "kind": "oracle",
-                   "sample": "%d pivots at z=0.5 of %s (neighbours from %d pixels); FP64 forward %.1fs + "
-                             "adjoint %.1fs; %d pairs" % (s["hi"] - s["lo"], wl.name, s["npts"], s["t_fwd"],
-                                                          s["t_bwd"], s["pairs"])}
-            zs, _ = plan.forward(d_dev, w_dev, (s["lo"], s["hi"]))
-            zg = tpcf.as_complex(zs).cpu().numpy()
-            zo = s["zeta"]
-            per_m = [float(np.abs(zg[m] - zo[m]).max() / max(np.abs(zo[m]).max(), 1e-300)) for m in range(M + 1)]
-            parity = {"pivots": s["hi"] - s["lo"], "max_rel_err_per_m": max(per_m), "tolerance": 1e-5}
+                   "sample": "%s; FP64 forward %.1fs + adjoint %.1fs; %d pairs" % (s["desc"], s["t_fwd"],
+                                                                                 s["t_bwd"], s["pairs"])}
+        a, b = W["split"]
+        parts = {a: {"ms": ms1 / args.steps}}
+        if b is not None:
+            parts[b] = {"ms": ms2 / args.steps}
         result = {
             "metric": METRIC,
             "value": value,
@@ -310,18 +536,10 @@ def run_gpu(args):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": wl.name, "nside": wl.nside, "npix": 12 * wl.nside * wl.nside,
-                       "bins": "%d %s bins %.2f-%.2f deg" % (K, "log" if wl.name != "map_nside64" else "lin",
-                                                             wl.bins.edges_deg[0], wl.bins.edges_deg[-1]),
-                       "m_max": M, "pass": "forward + adjoint", "pairs_per_step_per_gpu": total,
-                       "l2": "inputs larger than L2 (%.2f GB of (w d, w) per map)" % (8 * 12 * wl.nside ** 2 / 1e9),
-                       "parallelism": "independent map per GPU"},
-            "forward": {"ms": fwd_ms / args.steps, "pairs_per_s": world * total / (fwd_ms * 1e-3 / args.steps)},
-            "adjoint": {"ms": bwd_ms / args.steps},
-            "roofline": {"bound": "alu", "kernel": "map_bwd_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "forward_kernel_frac": (fwd_flops / fwd_s / 1e12) / peak},
-            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "config": W["config"],
+            "parts": parts,
+            "roofline": roof,
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -330,7 +548,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    plan.close()
+    W["close"]()
     return result
 
 
@@ -340,26 +558,33 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    wl = workload(args.workload)
-    d32, w32 = map_inputs(wl, 0)
+    if args.workload in MAP_WORKLOADS:
+        wl = map_workload(args.workload)
+        d32, w32 = map_inputs(wl, 0)
+        sample = lambda: oracle_sample(wl, d32, w32, args.ref_pivots)
+        cfg = {"workload": wl.name, "nside": wl.nside, "m_max": wl.bins.m_max, "pass": "forward + adjoint",
+               "sample_pivots": args.ref_pivots}
+    elif args.workload == "catalog_2e7":
+        wl, xu, du, wu, xr, _ = catalog_inputs(0)
+        sample = lambda: oracle_sample_catalog(xu, du, wu, wl.bins.edges_deg, wl.bins.m_max, args.ref_pivots)
+        cfg = {"workload": wl.name, "m_max": wl.bins.m_max, "pass": "D-R forward", "sample_pivots": args.ref_pivots}
+    else:
+        return {"impl": "reference", "unavailable": "the oracle arm covers the map and catalogue workloads"}
     vals = []
     s = None
     for k in range(args.warmup + args.steps):
-        s = oracle_sample(wl, d32, w32, args.ref_pivots)
+        s = sample()
         if k >= args.warmup:
             vals.append((s["pairs"], s["t_fwd"] + s["t_bwd"]))
     pairs = sum(v[0] for v in vals)
     secs = sum(v[1] for v in vals)
     value = pairs / secs
     cpu = {"value": value, "unit": "pairs/s", "cores": s["cores"], "kind": "oracle",
-           "sample": "%d pivots at z=0.5 of %s per step (FP64 forward + adjoint)" % (args.ref_pivots, wl.name)}
+           "sample": "%s per step" % s["desc"]}
     return {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl.name, "nside": wl.nside, "m_max": wl.bins.m_max, "pass": "forward + adjoint",
-                       "sample_pivots": args.ref_pivots},
-            "cpu_baseline": cpu,
+            "data": "synthetic", "impl": "reference", "config": cfg, "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -372,7 +597,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-pivots", type=int, default=2048)
     ap.add_argument("--ref-pivots", type=int, default=512)
+    ap.add_argument("--batch-nsides", default="256,512,1024,2048")
+    ap.add_argument("--contract", default="fp32", choices=["fp32", "tc"],
+                    help="contraction of the map forward: FP32 pipe or tensor cores (TF32x3)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 steps")

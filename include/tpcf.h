@@ -61,7 +61,9 @@ typedef enum {
 #define TPCF_SELF_PAIRS_SUBTRACT 1u  /* remove it from S_m(k,k) and from D(k,k)     */
 #define TPCF_CONTRACT_FP32 0u        /* sum over pivots on the FP32 pipe            */
 #define TPCF_CONTRACT_TC 2u          /* sum over pivots on the tensor cores (split
-                                        TF32x3 operands, FP32 accumulate)           */
+                                        TF32x3 operands, FP32 accumulate): map plans,
+                                        tpcf_forward only; catalogue plans, batches and
+                                        tpcf_forward_noalloc return UNSUPPORTED     */
 
 #define TPCF_MAX_BINS 32
 #define TPCF_MAX_M 16
@@ -100,8 +102,8 @@ tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const tpcf_bins*
  * (fp32 chord from hi/lo coordinates, FP64 decision within 2e-6 of an edge).  The
  * plan keeps its own sorted copy: d_xyz may be freed once the call has returned.
  * Forward calls take d_delta / d_w in the caller's point order, and pivot ranges are
- * ranges of caller indices.  The adjoint and the pair count are map-only
- * (TPCF_ERR_UNSUPPORTED).  1 <= n <= 2^31 - 1, else TPCF_ERR_INVALID_ARG.
+ * ranges of caller indices.  The adjoint is map-only (TPCF_ERR_UNSUPPORTED).
+ * 1 <= n <= 2^31 - 1, else TPCF_ERR_INVALID_ARG.
  */
 tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_xyz, int64_t n,
                                      const tpcf_bins* bins, void* stream);
@@ -172,8 +174,8 @@ tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const float* d_w
  * Exact number of in-bin ordered pairs (i, j) whose pivot i lies in
  * [pivot_begin, pivot_end) and has w_i != 0, whatever w_j (the units of the
  * throughput figure).  d_counts (device, int64[3]) receives: the total, the pairs
- * visited as mirror images (equatorial-belt symmetry), the pairs visited singly.
- * Map plans only.
+ * visited as mirror images (equatorial-belt symmetry), the pairs visited singly
+ * (catalogue plans visit every pair singly).
  */
 tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_t pivot_begin, int64_t pivot_end,
                              int64_t* d_counts, void* stream);

@@ -18,6 +18,8 @@ namespace tpcf {
 // per-M launchers (map_inst.cu)
 #define TPCF_DECL_M(m)                                                                      \
     cudaError_t map_fwd_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
+    cudaError_t map_fwd_tc_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);   \
+    int map_fwd_tc_occupancy_m##m(int, int);                                               \
     cudaError_t map_bwd_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
     int map_fwd_occupancy_m##m(int, int);                                                  \
     int map_bwd_occupancy_m##m(int);                                                       \
@@ -31,11 +33,15 @@ cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, l
                              unsigned long long* counts, int grid, cudaStream_t s);
 // catalogue plans (catalog.cu)
 tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaStream_t s);
+tpcf_status catalog_count(tpcf_plan_s* P, const float* d_w, int64_t lo, int64_t hi, int64_t* d_counts,
+                          cudaStream_t s);
 tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
                             double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s);
 
 struct MLaunch {
     cudaError_t (*fwd)(const MapDev&, const MapCall&, int, cudaStream_t);
+    cudaError_t (*fwd_tc)(const MapDev&, const MapCall&, int, cudaStream_t);
+    int (*fwd_tc_occ)(int, int);
     cudaError_t (*bwd)(const MapDev&, const MapCall&, int, cudaStream_t);
     int (*fwd_occ)(int, int);
     int (*bwd_occ)(int);
@@ -43,7 +49,7 @@ struct MLaunch {
     size_t (*bwd_smem)(int);
 };
 #define TPCF_ROW_M(m) \
-    {map_fwd_launch_m##m, map_bwd_launch_m##m, map_fwd_occupancy_m##m, map_bwd_occupancy_m##m, map_fwd_smem_m##m, map_bwd_smem_m##m}
+    {map_fwd_launch_m##m, map_fwd_tc_launch_m##m, map_fwd_tc_occupancy_m##m, map_bwd_launch_m##m, map_fwd_occupancy_m##m, map_bwd_occupancy_m##m, map_fwd_smem_m##m, map_bwd_smem_m##m}
 static const MLaunch kLaunch[TPCF_MAX_M + 1] = {
     TPCF_ROW_M(0),  TPCF_ROW_M(1),  TPCF_ROW_M(2),  TPCF_ROW_M(3),  TPCF_ROW_M(4),  TPCF_ROW_M(5),
     TPCF_ROW_M(6),  TPCF_ROW_M(7),  TPCF_ROW_M(8),  TPCF_ROW_M(9),  TPCF_ROW_M(10), TPCF_ROW_M(11),
@@ -172,7 +178,8 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     // per-call scratch, sized once so calls allocate nothing
     const MLaunch& L = kLaunch[P->M];
     const int self = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
-    int occ_f = L.fwd_occ(K, self);
+    const bool tc = (P->flags & TPCF_CONTRACT_TC) != 0;
+    int occ_f = tc ? L.fwd_tc_occ(K, self) : L.fwd_occ(K, self);
     int occ_b = L.bwd_occ(K);
     if (occ_f < 1 || occ_b < 1) {
         snprintf(g_last_error, sizeof(g_last_error), "kernel does not fit (K=%d, M=%d)", K, P->M);
@@ -232,6 +239,10 @@ extern "C" tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_
     *out = nullptr;
     if (!d_xyz || n < 1 || n > 0x7fffffffLL) return TPCF_ERR_INVALID_ARG;
     tpcf_status st = check_bins(bins);
+    if (st == TPCF_OK && (bins->flags & TPCF_CONTRACT_TC)) {
+        set_error("catalogue plans use the FP32 contraction");
+        return TPCF_ERR_UNSUPPORTED;
+    }
     if (st != TPCF_OK) return st;
     tpcf_plan_s* P = new (std::nothrow) tpcf_plan_s();
     if (!P) return TPCF_ERR_OOM;
@@ -283,7 +294,10 @@ static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float
     c.counter = P->counter;
     c.status = P->status;
     c.self_subtract = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
-    TRY_CUDA(kLaunch[P->M].fwd(g, c, P->fwd_grid, s));
+    if (P->flags & TPCF_CONTRACT_TC)
+        TRY_CUDA(kLaunch[P->M].fwd_tc(g, c, P->fwd_grid, s));
+    else
+        TRY_CUDA(kLaunch[P->M].fwd(g, c, P->fwd_grid, s));
     reduce_slots_kernel<<<n_blocks(P->nent, 128), 128, 0, s>>>(P->slots, P->fwd_grid, P->nent, P->sums);
     const int nout = (P->M + 1) * P->K * P->K;
     finalize_kernel<<<n_blocks(nout, 128), 128, 0, s>>>(P->sums, P->K, P->M, c.self_subtract, 1.0, d_zeta,
@@ -312,9 +326,10 @@ extern "C" tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_
                                         int64_t pivot_end, int64_t* d_counts, void* stream) {
     if (!plan || !d_w || !d_counts) return TPCF_ERR_INVALID_ARG;
     if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
-    if (plan->kind != PLAN_MAP) return TPCF_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
+    if (plan->kind == PLAN_CATALOG) return catalog_count(plan, d_w, pivot_begin, pivot_end, d_counts, s);
+    if (plan->kind != PLAN_MAP) return TPCF_ERR_UNSUPPORTED;
     const MapDev& g = plan->map;
     // only the weights matter: pack them with a zero field
     pack_kernel<<<plan->num_sms * 8, 256, 0, s>>>(d_w, d_w, plan->wdw, g.npix);
@@ -402,6 +417,10 @@ extern "C" tpcf_status tpcf_plan_sync(tpcf_plan plan) {
     TRY_CUDA(cudaStreamSynchronize(plan->last_stream));
     int st = 0;
     TRY_CUDA(cudaMemcpy(&st, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_TC_TIMEOUT_BIT) {
+        snprintf(g_last_error, sizeof(g_last_error), "device status 0x%x (tensor-core wait timed out)", st);
+        return TPCF_ERR_TIMEOUT;
+    }
     if (st & ST_BAD_TILE) {
         snprintf(g_last_error, sizeof(g_last_error), "device status 0x%x (bad tile table)", st);
         return TPCF_ERR_DEVICE;

@@ -270,6 +270,10 @@ extern "C" tpcf_status tpcf_batch_create(tpcf_batch* out, const tpcf_plan* plans
         }
         if (!d_delta[i] || !d_w[i] || !d_zeta[i] || !d_norm[i]) return TPCF_ERR_INVALID_ARG;
         if (with_bwd && (!d_dL_dzeta[i] || !d_grad[i])) return TPCF_ERR_INVALID_ARG;
+        if (P->flags & TPCF_CONTRACT_TC) {
+            set_error("batch members use the FP32 contraction (plan has TPCF_CONTRACT_TC)");
+            return TPCF_ERR_UNSUPPORTED;
+        }
         if (with_bwd && (P->flags & TPCF_SELF_PAIRS_SUBTRACT)) {
             set_error("adjoint with self-pair subtraction");
             return TPCF_ERR_UNSUPPORTED;

@@ -73,6 +73,160 @@ __host__ __device__ inline size_t cat_tile_bytes(int K) {
     return tile_floats<M>(K) * sizeof(float) + (size_t)NWARPS * TILE * (2 * sizeof(float4) + sizeof(float2));
 }
 
+// The lane's pivot: fp32 hi/lo position, local north / east basis and the FP64
+// position (kept for the rare exact bin decisions).
+struct CatPivot {
+    float hx, hy, hz, lx, ly, lz;
+    float nx, ny, nz, ex, ey;
+    double px, py, pz;
+};
+
+__device__ __forceinline__ CatPivot cat_pivot(double px, double py, double pz) {
+    CatPivot P;
+    P.px = px;
+    P.py = py;
+    P.pz = pz;
+    P.hx = (float)px;
+    P.hy = (float)py;
+    P.hz = (float)pz;
+    P.lx = (float)(px - (double)P.hx);
+    P.ly = (float)(py - (double)P.hy);
+    P.lz = (float)(pz - (double)P.hz);
+    const double s2 = px * px + py * py;
+    if (s2 > 1e-24) {
+        const double is = 1.0 / sqrt(s2);
+        P.ex = (float)(-py * is);  // east = z x n / |z x n|
+        P.ey = (float)(px * is);
+        P.nx = (float)(-pz * px * is);  // north = n x east
+        P.ny = (float)(-pz * py * is);
+        P.nz = (float)(s2 * is);
+    } else {  // on the axis: any tangent basis of the same handedness
+        P.ex = 0.0f;
+        P.ey = 1.0f;
+        P.nx = (float)(-pz);
+        P.ny = 0.0f;
+        P.nz = 0.0f;
+    }
+    return P;
+}
+
+// Warp 0: the bounding cap of the tile's live pivots (FP64) into s_cap = (centre,
+// query radius R + theta_max + CAT_EPS).  The caller synchronises afterwards.
+__device__ __forceinline__ void cat_tile_cap(const CatDev& g, bool live, double px, double py, double pz,
+                                             double* s_cap) {
+    double sx = live ? px : 0.0, sy = live ? py : 0.0, sz = live ? pz : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    double nrm = sqrt(sx * sx + sy * sy + sz * sz);
+    if (!(nrm > 1e-300)) {  // live pivots cancel out: any centre will do (r is measured from it)
+        sx = 0.0;
+        sy = 0.0;
+        sz = 1.0;
+        nrm = 1.0;
+    }
+    const double cx = sx / nrm, cy = sy / nrm, cz = sz / nrm;
+    double r = 0.0;
+    if (live) {
+        const double dx = px - cx, dy = py - cy, dz = pz - cz;
+        const double ch = sqrt(dx * dx + dy * dy + dz * dz);
+        r = 2.0 * asin(fmin(1.0, 0.5 * ch));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) {
+        s_cap[0] = cx;
+        s_cap[1] = cy;
+        s_cap[2] = cz;
+        s_cap[3] = r + g.theta_max + CAT_EPS;
+    }
+}
+
+// Every candidate of the cap for this warp (bands round-robin over the warps), with
+// its bin k (-1 below the first edge, K beyond the last), the chord vector from the
+// lane's pivot and its (w d, w): f(k, dx, dy, dz, v).  Candidates are staged 32 at a
+// time in the warp's shared buffers wh / wl / wv.
+template <class F>
+__device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restrict__ wdw, const double* s_cap,
+                                         const CatPivot& P, const float* sE2, const unsigned char* slut,
+                                         float4* wh, float4* wl, float2* wv, F&& f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = g.K;
+    const double cx = s_cap[0], cy = s_cap[1], cz = s_cap[2], Q = s_cap[3];
+    const double thc = atan2(sqrt(cx * cx + cy * cy), cz);
+    double phc = atan2(cy, cx);
+    if (phc < 0.0) phc += 2.0 * M_PI;
+    int b0 = 0, b1 = g.nbands - 1;
+    bool full = true;
+    double dphi = M_PI;
+    if (Q < M_PI) {
+        b0 = max(0, (int)floor((thc - Q) / g.hband));
+        b1 = min(g.nbands - 1, (int)floor((thc + Q) / g.hband));
+        // longitude half-width of the cap, valid for every colatitude it reaches
+        const double sq = sin(Q), st = sin(thc);
+        if (thc - Q > 0.0 && thc + Q < M_PI && sq < st) {
+            full = false;
+            dphi = asin(sq / st) + CAT_EPS;
+        }
+    }
+    for (int b = b0 + warp; b <= b1; b += NWARPS) {
+        const int64_t ns = g.band_ns[b];
+        const int64_t cf = g.band_first[b];
+        // at most two cell ranges (the sector range may wrap around phi = 0)
+        int64_t ca0 = cf, ca1 = cf + ns, cb0 = 0, cb1 = 0;
+        if (!full) {
+            const double scale = (double)ns / (2.0 * M_PI);
+            const int64_t sa = (int64_t)floor((phc - dphi) * scale);
+            const int64_t sb = (int64_t)floor((phc + dphi) * scale);
+            const int64_t len = sb - sa + 1;
+            if (len < ns) {
+                int64_t s0 = sa % ns;
+                if (s0 < 0) s0 += ns;
+                ca0 = cf + s0;
+                if (s0 + len <= ns) {
+                    ca1 = cf + s0 + len;
+                } else {
+                    ca1 = cf + ns;
+                    cb0 = cf;
+                    cb1 = cf + (s0 + len - ns);
+                }
+            }
+        }
+#pragma unroll 1
+        for (int sg = 0; sg < 2; ++sg) {
+            const int64_t cl0 = sg == 0 ? ca0 : cb0, cl1 = sg == 0 ? ca1 : cb1;
+            if (cl1 <= cl0) continue;
+            const int64_t p0 = g.cell_start[cl0], p1 = g.cell_start[cl1];
+            for (int64_t base = p0; base < p1; base += TILE) {
+                const int64_t j = base + lane;
+                __syncwarp();
+                if (j < p1) {
+                    wh[lane] = g.p_hi[j];
+                    wl[lane] = g.p_lo[j];
+                    wv[lane] = wdw[j];
+                }
+                __syncwarp();
+                const int cnt = (int)min((int64_t)TILE, p1 - base);
+                for (int u = 0; u < cnt; ++u) {
+                    const float4 qh = wh[u], ql = wl[u];
+                    const float dx = (qh.x - P.hx) + (ql.x - P.lx);
+                    const float dy = (qh.y - P.hy) + (ql.y - P.ly);
+                    const float dz = (qh.z - P.hz) + (ql.z - P.lz);
+                    const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
+                    const int e1 = max(k, 0), e2 = min(k + 1, K);
+                    if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
+                        k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.px, P.py, P.pz);
+                    f(k, dx, dy, dz, wv[u]);
+                }
+            }
+        }
+    }
+}
+
 template <int M, bool SELF>
 __global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall c) {
     extern __shared__ __align__(16) float smem[];
@@ -94,9 +248,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall 
     for (int e = threadIdx.x; e <= K; e += NTHREADS) sE2[e] = g.E2[e];
     for (int e = threadIdx.x; e < CAT_LUT; e += NTHREADS) slut[e] = g.lut[e];
     double* slot = c.slots + (size_t)blockIdx.x * n_entries(K, M);
-    float4* wh = sCh + warp * TILE;
-    float4* wl = sCl + warp * TILE;
-    float2* wv = sCv + warp * TILE;
 
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
@@ -124,84 +275,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall 
             sPiv[lane] = pv.x;
             sPiv[TILE + lane] = pv.y;
         }
-        if (warp == 0) {
-            // bounding cap of the live pivots, in fp64
-            double sx = live ? px : 0.0, sy = live ? py : 0.0, sz = live ? pz : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                sz += __shfl_xor_sync(0xffffffffu, sz, o);
-            }
-            double nrm = sqrt(sx * sx + sy * sy + sz * sz);
-            if (!(nrm > 1e-300)) {  // live pivots cancel out: any centre will do (r is measured from it)
-                sx = 0.0;
-                sy = 0.0;
-                sz = 1.0;
-                nrm = 1.0;
-            }
-            const double cx = sx / nrm, cy = sy / nrm, cz = sz / nrm;
-            double r = 0.0;
-            if (live) {
-                const double dx = px - cx, dy = py - cy, dz = pz - cz;
-                const double ch = sqrt(dx * dx + dy * dy + dz * dz);
-                r = 2.0 * asin(fmin(1.0, 0.5 * ch));
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-            if (lane == 0) {
-                s_cap[0] = cx;
-                s_cap[1] = cy;
-                s_cap[2] = cz;
-                s_cap[3] = r + g.theta_max + CAT_EPS;
-            }
-        }
+        if (warp == 0) cat_tile_cap(g, live, px, py, pz, s_cap);
         __syncthreads();
-
-        // the lane's pivot: fp32 hi/lo position and local north / east basis
-        float hx = 0.0f, hy = 0.0f, hz = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
-        float nx, ny, nz, ex, ey;
-        {
-            hx = (float)px;
-            hy = (float)py;
-            hz = (float)pz;
-            lx = (float)(px - (double)hx);
-            ly = (float)(py - (double)hy);
-            lz = (float)(pz - (double)hz);
-            const double s2 = px * px + py * py;
-            if (s2 > 1e-24) {
-                const double is = 1.0 / sqrt(s2);
-                ex = (float)(-py * is);  // east = z x n / |z x n|
-                ey = (float)(px * is);
-                nx = (float)(-pz * px * is);  // north = n x east
-                ny = (float)(-pz * py * is);
-                nz = (float)(s2 * is);
-            } else {  // on the axis: any tangent basis of the same handedness
-                ex = 0.0f;
-                ey = 1.0f;
-                nx = (float)(-pz);
-                ny = 0.0f;
-                nz = 0.0f;
-            }
-        }
-
-        // cells within the query cap: band range and longitude half-width
-        const double cx = s_cap[0], cy = s_cap[1], cz = s_cap[2], Q = s_cap[3];
-        const double thc = atan2(sqrt(cx * cx + cy * cy), cz);
-        double phc = atan2(cy, cx);
-        if (phc < 0.0) phc += 2.0 * M_PI;
-        int b0 = 0, b1 = g.nbands - 1;
-        bool full = true;
-        double dphi = M_PI;
-        if (Q < M_PI) {
-            b0 = max(0, (int)floor((thc - Q) / g.hband));
-            b1 = min(g.nbands - 1, (int)floor((thc + Q) / g.hband));
-            const double sq = sin(Q), st = sin(thc);
-            if (thc - Q > 0.0 && thc + Q < M_PI && sq < st) {
-                full = false;
-                dphi = asin(sq / st) + CAT_EPS;
-            }
-        }
+        const CatPivot P = cat_pivot(px, py, pz);
 
         float re[M + 1], im[M + 1];
 #pragma unroll
@@ -211,80 +287,78 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall 
         }
         float W = 0.0f, Qs = 0.0f, QW = 0.0f;
         int kcur = -1;
-        for (int b = b0 + warp; b <= b1; b += NWARPS) {
-            const int64_t ns = g.band_ns[b];
-            const int64_t cf = g.band_first[b];
-            // at most two cell ranges (the sector range may wrap around phi = 0)
-            int64_t ca0 = cf, ca1 = cf + ns, cb0 = 0, cb1 = 0;
-            if (!full) {
-                const double scale = (double)ns / (2.0 * M_PI);
-                const int64_t sa = (int64_t)floor((phc - dphi) * scale);
-                const int64_t sb = (int64_t)floor((phc + dphi) * scale);
-                const int64_t len = sb - sa + 1;
-                if (len < ns) {
-                    int64_t s0 = sa % ns;
-                    if (s0 < 0) s0 += ns;
-                    ca0 = cf + s0;
-                    if (s0 + len <= ns) {
-                        ca1 = cf + s0 + len;
-                    } else {
-                        ca1 = cf + ns;
-                        cb0 = cf;
-                        cb1 = cf + (s0 + len - ns);
-                    }
-                }
-            }
-#pragma unroll 1
-            for (int sg = 0; sg < 2; ++sg) {
-                const int64_t cl0 = sg == 0 ? ca0 : cb0, cl1 = sg == 0 ? ca1 : cb1;
-                if (cl1 <= cl0) continue;
-                const int64_t p0 = g.cell_start[cl0], p1 = g.cell_start[cl1];
-                for (int64_t base = p0; base < p1; base += TILE) {
-                    const int64_t j = base + lane;
-                    __syncwarp();
-                    if (j < p1) {
-                        wh[lane] = g.p_hi[j];
-                        wl[lane] = g.p_lo[j];
-                        wv[lane] = c.wdw[j];
-                    }
-                    __syncwarp();
-                    const int cnt = (int)min((int64_t)TILE, p1 - base);
-                    for (int u = 0; u < cnt; ++u) {
-                        const float4 qh = wh[u], ql = wl[u];
-                        const float2 v = wv[u];
-                        const float dx = (qh.x - hx) + (ql.x - lx);
-                        const float dy = (qh.y - hy) + (ql.y - ly);
-                        const float dz = (qh.z - hz) + (ql.z - lz);
-                        const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
-                        const int e1 = max(k, 0), e2 = min(k + 1, K);
-                        if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
-                            k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), px, py, pz);
-                        const bool on = k >= 0 && k < K;
-                        if (on && k != kcur) {
-                            if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, re, im, W, Qs, QW);
-                            kcur = k;
-                        }
-                        const float N = fmaf(dx, nx, fmaf(dy, ny, dz * nz));
-                        const float E = fmaf(dx, ex, dy * ey);
-                        const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
-                        const float wd = on ? v.x : 0.0f;
-                        const float ww = on ? v.y : 0.0f;
-                        harmonics<M>(re, im, N * rinv, E * rinv, wd, wd);
-                        W += ww;
-                        if (SELF) {
-                            Qs = fmaf(wd, wd, Qs);
-                            QW = fmaf(ww, ww, QW);
-                        }
-                    }
-                }
-            }
-        }
+        cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+                 [&](int k, float dx, float dy, float dz, float2 v) {
+                     const bool on = k >= 0 && k < K;
+                     if (on && k != kcur) {
+                         if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, re, im, W, Qs, QW);
+                         kcur = k;
+                     }
+                     const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                     const float E = fmaf(dx, P.ex, dy * P.ey);
+                     const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                     const float wd = on ? v.x : 0.0f;
+                     const float ww = on ? v.y : 0.0f;
+                     harmonics<M>(re, im, N * rinv, E * rinv, wd, wd);
+                     W += ww;
+                     if (SELF) {
+                         Qs = fmaf(wd, wd, Qs);
+                         QW = fmaf(ww, ww, QW);
+                     }
+                 });
         if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, re, im, W, Qs, QW);
         __syncthreads();
         tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
         __syncthreads();
     }
 }
+
+#if defined(TPCF_M) && TPCF_M == 0  // one definition, in the M = 0 object
+// Exact number of in-bin ordered pairs (i, j) with w_i != 0 and caller index of i in
+// [lo, hi): counts[0] += total.  Same tiles and candidate walk as the forward.
+__global__ void __launch_bounds__(NTHREADS) cat_count_kernel(CatDev g, const float2* __restrict__ wdw, long long lo,
+                                                             long long hi, int* counter,
+                                                             unsigned long long* counts) {
+    __shared__ int s_tile;
+    __shared__ double s_cap[4];
+    __shared__ float sE2[TPCF_MAX_BINS + 1];
+    __shared__ unsigned char slut[CAT_LUT];
+    __shared__ __align__(16) float4 sCh[NWARPS * TILE];
+    __shared__ __align__(16) float4 sCl[NWARPS * TILE];
+    __shared__ __align__(16) float2 sCv[NWARPS * TILE];
+    const int K = g.K;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e <= K; e += NTHREADS) sE2[e] = g.E2[e];
+    for (int e = threadIdx.x; e < CAT_LUT; e += NTHREADS) slut[e] = g.lut[e];
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if ((long long)tile >= g.ntiles) break;
+        const int64_t si = (int64_t)tile * TILE + lane;
+        bool live = false;
+        double px = 0.0, py = 0.0, pz = 1.0;
+        if (si < g.n) {
+            const int64_t o = g.orig[si];
+            live = o >= lo && o < hi && wdw[si].y != 0.0f;
+            px = g.xyz[3 * si];
+            py = g.xyz[3 * si + 1];
+            pz = g.xyz[3 * si + 2];
+        }
+        if (!__syncthreads_or(live)) continue;
+        if (warp == 0) cat_tile_cap(g, live, px, py, pz, s_cap);
+        __syncthreads();
+        const CatPivot P = cat_pivot(px, py, pz);
+        unsigned long long cnt = 0;
+        cat_walk(g, wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+                 [&](int k, float, float, float, float2) { cnt += (k >= 0 && k < K) ? 1ull : 0ull; });
+        cnt = live ? cnt : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(counts, cnt);
+        __syncthreads();
+    }
+}
+#endif
 
 }  // namespace tpcf

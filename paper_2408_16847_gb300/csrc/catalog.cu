@@ -63,7 +63,7 @@ __device__ __forceinline__ int64_t cat_cell_of(double x, double y, double z, int
     return band_first[b] + s;
 }
 
-__global__ void cat_count_kernel(int64_t n, const double* __restrict__ xyz, int nb, double hb,
+__global__ void cat_cell_count_kernel(int64_t n, const double* __restrict__ xyz, int nb, double hb,
                                  const int64_t* band_first, const int64_t* band_ns, int64_t* cell,
                                  unsigned long long* count) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -197,7 +197,7 @@ tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaSt
     e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long) * (ncells + 1), s);
     if (e == cudaSuccess) {
         const int grid = P->num_sms * 8;
-        cat_count_kernel<<<grid, 256, 0, s>>>(n, d_xyz, nb, g.hband, band_first, band_ns, cell, cursor);
+        cat_cell_count_kernel<<<grid, 256, 0, s>>>(n, d_xyz, nb, g.hband, band_first, band_ns, cell, cursor);
         exclusive_scan_kernel<<<1, 1024, 0, s>>>((const int64_t*)cursor, cell_start, (int)ncells, cell_start + ncells);
         e = cudaMemcpyAsync(cursor, cell_start, sizeof(int64_t) * (ncells + 1), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
@@ -234,6 +234,23 @@ tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaSt
     TRY_CUDA(P->alloc(&P->status, 4));
     TRY_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int) * 4, s));
     TRY_CUDA(cudaStreamSynchronize(s));
+    return TPCF_OK;
+}
+
+cudaError_t cat_count_launch(const CatDev& g, const float2* wdw, long long lo, long long hi, int* counter,
+                             unsigned long long* counts, int grid, cudaStream_t s);
+
+tpcf_status catalog_count(tpcf_plan_s* P, const float* d_w, int64_t lo, int64_t hi, int64_t* d_counts,
+                          cudaStream_t s) {
+    const CatDev& g = P->cat;
+    // only the weights matter: pack them with a zero field
+    cat_pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(g.n, g.orig, d_w, d_w, P->wdw);
+    P->launches += 2;
+    TRY_CUDA(cudaMemsetAsync(d_counts, 0, 3 * sizeof(int64_t), s));
+    TRY_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(int), s));
+    TRY_CUDA(cat_count_launch(g, P->wdw, lo, hi, P->counter, (unsigned long long*)d_counts, P->num_sms * 4, s));
+    // every catalogue pair is visited singly: counts[2] = counts[0]
+    TRY_CUDA(cudaMemcpyAsync(d_counts + 2, d_counts, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     return TPCF_OK;
 }
 

@@ -61,6 +61,44 @@ int TPCF_CAT(map_bwd_occupancy_m, TPCF_M)(int K) {
     return nb;
 }
 
+// Forward with the split-precision tensor-core contraction.
+static size_t fwd_tc_smem(int K) {
+    const size_t a = tc_region_bytes(K) + tile_floats<TPCF_M>(K) * sizeof(float);
+    const size_t b = tc_min_total_bytes(K);
+    return a > b ? a : b;
+}
+
+cudaError_t TPCF_CAT(map_fwd_tc_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid, cudaStream_t s) {
+    const size_t smem = fwd_tc_smem(g.K);
+    if (c.self_subtract) {
+        auto* k = map_fwd_tc_kernel<TPCF_M, true>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    } else {
+        auto* k = map_fwd_tc_kernel<TPCF_M, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    }
+    return cudaGetLastError();
+}
+
+int TPCF_CAT(map_fwd_tc_occupancy_m, TPCF_M)(int K, int self_subtract) {
+    const size_t smem = fwd_tc_smem(K);
+    int nb = 0;
+    if (self_subtract) {
+        cudaFuncSetAttribute(map_fwd_tc_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_tc_kernel<TPCF_M, true>, NTHREADS, smem);
+    } else {
+        cudaFuncSetAttribute(map_fwd_tc_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_tc_kernel<TPCF_M, false>, NTHREADS, smem);
+    }
+    // at most 512 / TC_TMEM_COLS accumulators per SM; more resident CTAs would wait in tcgen05.alloc
+    return nb < 512 / TC_TMEM_COLS ? nb : 512 / TC_TMEM_COLS;
+}
+
 // Forward that reads the caller's delta and w directly (no packed copy).
 cudaError_t TPCF_CAT(map_fwd_direct_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid,
                                                       cudaStream_t s) {
@@ -155,6 +193,12 @@ int TPCF_CAT(cat_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
 }
 
 #if TPCF_M == 0
+cudaError_t cat_count_launch(const CatDev& g, const float2* wdw, long long lo, long long hi, int* counter,
+                             unsigned long long* counts, int grid, cudaStream_t s) {
+    cat_count_kernel<<<grid, NTHREADS, 0, s>>>(g, wdw, lo, hi, counter, counts);
+    return cudaGetLastError();
+}
+
 cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi,
                              unsigned long long* counts, int grid, cudaStream_t s) {
     map_count_kernel<<<grid, NTHREADS, 0, s>>>(g, wdw, lo, hi, counts);

@@ -575,10 +575,242 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
     }
 }
 
+// ------------------------------------------------- tensor-core contraction (TF32x3)
+// The contraction of eq. zetamEst2 over a tile's 32 pivots is, for each m, the Gram
+// matrix G = X diag(w d) X^T of X = [Re a ; Im a] (rows r = 2k + part, 32 pivot
+// columns): S_m(k1,k2) = G[2k1][2k2] + G[2k1+1][2k2+1] + i (G[2k1][2k2+1] - G[2k1+1][2k2])
+// in the convention a = re - i im.  D is the same product of the W^k rows with the
+// weights w.  On the 5th-generation tensor cores, per m:
+//   D[128 x N] = A[128 x 32] . B[N x 32]^T,  kind::tf32, FP32 accumulate in TMEM,
+// A = X diag(w d) and B = X in shared memory (K-major, no swizzle: 8-row x 16-byte
+// core matrices, K-adjacent ones 128 B apart, 8-row groups 1024 B apart).  Each
+// operand is split into a tf32 part and its fp32 remainder, and the three products
+// hi.hi + hi.lo + lo.hi run into the same accumulator (TF32x3; the dropped lo.lo term
+// is below 2^-22 relative).  A has 128 rows but only 2K are written: the MMA reads its
+// other rows from whatever follows in shared memory, which only reaches accumulator
+// rows that are never read.  One thread issues; completion is tracked by an mbarrier
+// with a bounded wait; warps 0-1 read the accumulator rows back and add the S and D
+// entries into the CTA's FP64 slot.
+constexpr int TC_TMEM_COLS = 64;              // accumulator columns (N <= 64)
+constexpr int TC_A_WINDOW = 16 * 1024;        // bytes the MMA reads from A (128 rows x 128 B)
+constexpr int ST_TC_TIMEOUT = ST_TC_TIMEOUT_BIT;
+
+__host__ __device__ inline int tc_rows(int K) { return (2 * K + 15) & ~15; }
+__host__ __device__ inline size_t tc_operand_bytes(int K) { return (size_t)tc_rows(K) * 128; }
+// Shared memory of the TC operands (placed first) and the padding that keeps the
+// 16 KB window read from A_lo inside the allocation.
+__host__ __device__ inline size_t tc_region_bytes(int K) { return 4 * tc_operand_bytes(K); }
+__host__ __device__ inline size_t tc_min_total_bytes(int K) { return tc_operand_bytes(K) + TC_A_WINDOW; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// UMMA shared-memory descriptor: start address, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor: D f32, A and B tf32, both K-major, N, M = 128.
+__device__ __forceinline__ uint32_t tc_idesc(int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Byte offset of element (row r, pivot p) in a K-major no-swizzle operand.
+__device__ __forceinline__ uint32_t tc_off(int r, int p) {
+    return (uint32_t)((((r >> 3) * 8 + (p >> 2)) << 7) + ((r & 7) << 4) + ((p & 3) << 2));
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// Waits for the mbarrier phase; false after about one second (error path).
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Per-CTA tensor-core state: TMEM accumulator base, mbarrier and its phase.
+struct TcState {
+    uint32_t tmem;
+    uint32_t mbar;    // shared address of the mbarrier
+    uint32_t phase;
+    int* fail;        // shared flag: a wait gave up
+};
+
+// Warp 0 allocates the accumulator columns; thread 0 initialises the mbarrier.
+__device__ __forceinline__ void tc_setup(uint32_t* s_tmem, uint64_t* s_mbar) {
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+// The tile's S and D partial sums on the tensor cores (see above); the self-pair
+// diagonals stay on the FP32 pipe.  tcbuf: the operand region (tc_region_bytes).
+template <int M>
+__device__ void tile_contract_tc(int K, const float* sA, const float* sW, const float* sQ, const float* sQW,
+                                 const float* sPiv, double* slot, bool self, float* tcbuf, TcState& tc,
+                                 int* status) {
+    const int P = n_pairs_tri(K);
+    const int nS = (M + 1) * P;
+    const int R2 = 2 * K;
+    const int opw = (int)(tc_operand_bytes(K) / 4);
+    float* Ahi = tcbuf;
+    float* Alo = Ahi + opw;
+    float* Bhi = Alo + opw;
+    float* Blo = Bhi + opw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int mm = 0; mm <= M + 1; ++mm) {
+        const bool isD = mm == M + 1;  // the D Gram: rows W^k, weights w
+        const int rows = isD ? K : R2;
+        const int Nn = (rows + 15) & ~15;
+        for (int e = threadIdx.x; e < Nn * TILE; e += NTHREADS) {
+            // consecutive threads write consecutive words of the core-matrix layout
+            const int r = ((e >> 8) << 3) + ((e >> 2) & 7);
+            const int p = (((e >> 5) & 7) << 2) + (e & 3);
+            float x = 0.0f;
+            if (r < rows)
+                x = isD ? sW[r * TILE + p] : sA[((size_t)((r >> 1) * (M + 1) + mm) * 2 + (r & 1)) * TILE + p];
+            const float a = x * (isD ? sPiv[TILE + p] : sPiv[p]);
+            const float ah = tf32_rna(a), xh = tf32_rna(x);
+            Ahi[e] = ah;
+            Alo[e] = a - ah;
+            Bhi[e] = xh;
+            Blo[e] = x - xh;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = tc_idesc(Nn);
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll
+            for (int k8 = 0; k8 < TILE / 8; ++k8) {
+                const uint32_t o = (uint32_t)k8 * 256u;  // two K-adjacent core matrices per k-step
+                tc_mma(tc.tmem, tc_sdesc(ah + o), tc_sdesc(bh + o), idesc, k8 > 0);
+                tc_mma(tc.tmem, tc_sdesc(ah + o), tc_sdesc(bl + o), idesc, 1);
+                tc_mma(tc.tmem, tc_sdesc(al + o), tc_sdesc(bh + o), idesc, 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc.mbar)
+                         : "memory");
+            if (!tc_wait(tc.mbar, tc.phase)) {
+                *tc.fail = 1;
+                atomicOr(status, ST_TC_TIMEOUT);
+            }
+        }
+        tc.phase ^= 1u;
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (*tc.fail) return;
+        if (warp * 32 < rows) {
+            const int r = warp * 32 + lane;
+            for (int c0 = 0; c0 < Nn; c0 += 16) {
+                float v[16];
+                tc_ld16(tc.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                if (isD) {
+                    if (r < K) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int k2 = c0 + j;
+                            if (k2 >= r && k2 < K) slot[2 * nS + k2 * (k2 + 1) / 2 + r] += (double)v[j];
+                        }
+                    }
+                } else {
+                    float u[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) u[j] = __shfl_down_sync(0xffffffffu, v[j], 1);
+                    if ((r & 1) == 0 && r < R2) {
+                        const int k1 = r >> 1;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int k2 = (c0 >> 1) + j;
+                            if (k2 >= k1 && k2 < K) {
+                                const int e = mm * P + k2 * (k2 + 1) / 2 + k1;
+                                slot[2 * e] += (double)(v[2 * j] + u[2 * j + 1]);
+                                slot[2 * e + 1] += (double)(v[2 * j + 1] - u[2 * j]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (self) {
+        const float* wd = sPiv;
+        const float* wt = sPiv + TILE;
+        for (int k = threadIdx.x; k < K; k += NTHREADS) {
+            float s1 = 0.0f, s2 = 0.0f;
+            for (int j = 0; j < TILE; ++j) {
+                s1 = fmaf(wd[j], sQ[k * TILE + j], s1);
+                s2 = fmaf(wt[j], sQW[k * TILE + j], s2);
+            }
+            slot[2 * nS + P + k] += (double)s1;
+            slot[2 * nS + P + K + k] += (double)s2;
+        }
+    }
+}
+
 // One forward tile: the moments of its 32 pivots, then their partial sums added to
 // the CTA's slot.  Called by every thread of the CTA (contains barriers).
-template <int M, bool SELF, bool DIRECT>
-__device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem) {
+template <int M, bool SELF, bool DIRECT, bool TC = false>
+__device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem,
+                                         float* tcbuf = nullptr, TcState* tc = nullptr) {
     const int K = g.K;
     float* sA = smem;
     float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
@@ -614,7 +846,10 @@ __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int 
     else
         tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
     __syncthreads();
-    tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+    if constexpr (TC)
+        tile_contract_tc<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF, tcbuf, *tc, c.status);
+    else
+        tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
     __syncthreads();
 }
 
@@ -630,6 +865,31 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall 
         if ((long long)tile >= g.ntiles) break;
         fwd_tile<M, SELF, DIRECT>(g, c, tile, slot, smem);
     }
+}
+
+// The forward with the tensor-core contraction: the dynamic shared memory starts
+// with the operand region (tc_region_bytes), the tile's arrays follow.
+template <int M, bool SELF>
+__global__ void __launch_bounds__(NTHREADS, 2) map_fwd_tc_kernel(MapDev g, MapCall c) {
+    extern __shared__ __align__(16) float smem_tc[];
+    __shared__ int s_tile;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    tc_setup(&s_tmem, &s_mbar);
+    TcState tc{s_tmem, smem_u32(&s_mbar), 0u, &s_fail};
+    float* tcbuf = smem_tc;
+    float* tile_smem = smem_tc + tc_region_bytes(g.K) / 4;
+    double* slot = c.slots + (size_t)blockIdx.x * n_entries(g.K, M);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if ((long long)tile >= g.ntiles || s_fail) break;
+        fwd_tile<M, SELF, false, true>(g, c, tile, slot, tile_smem, tcbuf, &tc);
+    }
+    tc_teardown(s_tmem);
 }
 
 // Batched forward over the plans of a batch that share M: one work queue over the

@@ -80,6 +80,10 @@ extern "C" tpcf_status tpcf_forward_noalloc(tpcf_plan plan, const float* d_delta
         set_error("tpcf_forward_noalloc: map plans only");
         return TPCF_ERR_UNSUPPORTED;
     }
+    if (plan->flags & TPCF_CONTRACT_TC) {
+        set_error("tpcf_forward_noalloc: FP32 contraction only");
+        return TPCF_ERR_UNSUPPORTED;
+    }
     if (plan->flags & TPCF_SELF_PAIRS_SUBTRACT) {
         set_error("tpcf_forward_noalloc: self-pair subtraction is not available here");
         return TPCF_ERR_UNSUPPORTED;

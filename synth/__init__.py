@@ -215,6 +215,13 @@ def fullsky_nside4096() -> MapWorkload:
                        seed=BASE_SEED + 5, cot_seed=BASE_SEED + 105)
 
 
+def fullsky_nside512() -> MapWorkload:
+    """The full-sky recipe at Nside 512 (bumps scaled by pixel count: 15,625): the
+    small case profiled in place of the Nside 4096 map."""
+    return MapWorkload("fullsky_nside512", 512, log_bins(0.1, 2.0, 20, 10), 15_625, (0.05, 1.0),
+                       seed=BASE_SEED + 6, cot_seed=BASE_SEED + 106)
+
+
 def batched_maps(n_maps: int = 64, nsides=(256, 512, 1024, 2048)) -> List[MapWorkload]:
     """64 independent maps, 16 each at Nside 256/512/1024/2048; one bump per 629 pixels;
     K ~ U{8..24} bins over 0.2-4 deg, lin/log alternating; m_max ~ U{6..12}."""

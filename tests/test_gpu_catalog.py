@@ -148,3 +148,18 @@ def test_edge_corrected_data_minus_randoms():
     # and the oracle's own D-R composition (alpha in fp64) agrees with that up to the
     # float32 rounding of alpha, amplified by the D-R cancellation
     assert rel_err_per_m(zo, ref["zeta"]).max() < 1e-4
+
+
+def test_catalogue_pair_count_exact():
+    tpcf = _tpcf()
+    xyz = synth.clustered_catalog(15000, 200, 0.7, synth.BASE_SEED + 970)
+    w = synth.rng(971).uniform(0.5, 1.5, len(xyz)).astype(np.float32)
+    w[::5] = 0.0
+    edges = np.linspace(0.3, 3.1, 8)
+    plan = tpcf.Plan.catalog(_xyz_dev(xyz), edges, 4)
+    total, sym, single = plan.count_pairs(to_dev(w))
+    live = np.nonzero(w)[0]
+    assert total == int(oracle.pair_counts(xyz, edges, pivots=live).sum())
+    assert sym == 0 and single == total
+    t2, _, _ = plan.count_pairs(to_dev(np.ones_like(w)), (1000, 4000))
+    assert t2 == int(oracle.pair_counts(xyz, edges, pivots=np.arange(1000, 4000)).sum())
