@@ -5,12 +5,13 @@ import torch
 import oracle
 from paper_2408_16847_gb300 import tpcf
 
-# Parity bar: max |zeta_gpu - zeta_oracle| <= TOL * max |zeta_oracle|.  The small
-# workloads meet it per multipole m (each m against its own largest entry).  At full
-# size the bar is read against the largest |zeta| of the estimate: there fp32 term
-# rounding (~1e-7 rad in the position angle) sets an absolute floor that, for m >= 9 in
-# the innermost bins of a few hundred sampled pivots, exceeds 1e-5 of that multipole's
-# own largest entry; TOL_PER_M_FULL bounds that per-m figure.
+# Parity bar: max |zeta_gpu - zeta_oracle| <= TOL * max |zeta_oracle| over the whole
+# estimate (all m, k1, k2).  Per multipole m, against that m's own largest entry, the
+# small map workloads also stay below TOL; where the high-m signal is small (full-size
+# maps with a few hundred sampled pivots, white-noise catalogues with self-pair
+# subtraction) the per-m figure reaches the fp32 floor of the pair arithmetic (the
+# Chebyshev recurrence and the position angle, ~1e-5 at m = 8..10) and is bounded by
+# TOL_PER_M_FULL instead.
 TOL = 1e-5
 TOL_PER_M_FULL = 5e-5
 
