@@ -119,6 +119,20 @@ def cat_flops_per_pair(M: int):
     return 35 + 6 * max(M - 1, 0)
 
 
+# DRAM bytes per pixel per launch of the map kernels, from the ncu capture of the
+# Nside 512 case (profiles/map_kernels_fullsky_nside512.md: dram__bytes_read.sum +
+# dram__bytes_write.sum / pixels), valid only for the kernel source it was taken on.
+TRAFFIC = {"map_bwd_kernel": (17.65, "93047a5ee754fbff"), "map_fwd_kernel": (17.62, "93047a5ee754fbff")}
+
+
+def traffic_per_launch(kernel, npix):
+    import hashlib
+    bpp, sha = TRAFFIC[kernel]
+    src = os.path.join(ROOT, "paper_2408_16847_gb300", "csrc", "map_kernels.cuh")
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return bpp * npix if cur == sha else None
+
+
 def fp32_peak_tflops(clk):
     return SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
 
@@ -290,6 +304,8 @@ def setup_map(args, dev, rank):
                     "bound": "alu", "kernel": "map_bwd_kernel",
                     "achieved": (fwd_flops + adj_flops) / (t2 * 1e-3) / 1e12,  # adjoint recomputes the forward
                     "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s",
+                    "traffic": traffic_per_launch("map_bwd_kernel", 12 * wl.nside ** 2),
+                    "traffic_note": "DRAM bytes per launch scaled by pixels from the Nside 512 ncu capture",
                     "forward_kernel_tflops": fwd_flops / (t1 * 1e-3) / 1e12},
                 small_l2=12 * wl.nside ** 2 * 8 <= 129e6, close=plan.close)
 
@@ -509,7 +525,7 @@ def run_gpu(args):
     if rank == 0:
         roof = W["roofline"](ms1 / args.steps, ms2 / args.steps, clk)
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
+        roof.setdefault("traffic", None)
         cpu = None
         parity = None
         if world == 1 and args.cpu_baseline and W["cpu_baseline"] is not None:
