@@ -253,14 +253,21 @@ def setup_map(args, dev, rank):
     cot = wl.cotangent()
     g_dev = torch.zeros((M + 1, K, K, 2), dtype=torch.float64, device=dev)
     g_dev[..., 0] = torch.from_numpy(cot).to(dev)
-    total, n_sym, n_single = plan.count_pairs(w_dev)
+    piv = None
+    if args.profile_band:
+        # pivots of `profile_band` belt rings from z = 1/2: the full-resolution kernels on a
+        # slice small enough for an ncu capture (not a bench number)
+        n = wl.nside
+        first = 2 * n * (n - 1) + 4 * n * ((5 * n) // 4 - n)
+        piv = (first, first + 4 * n * args.profile_band)
+    total, n_sym, n_single = plan.count_pairs(w_dev, piv)
     state = {}
 
     def step(ev=None):
-        zeta, norm = plan.forward(d_dev, w_dev)
+        zeta, norm = plan.forward(d_dev, w_dev, piv)
         if ev is not None:
             ev.record(torch.cuda.current_stream())
-        state["grad"] = plan.backward(d_dev, w_dev, norm, g_dev)
+        state["grad"] = plan.backward(d_dev, w_dev, norm, g_dev, piv)
 
     # e2e: the public host-buffer call, with its copies inside the timed region
     h_d = torch.from_numpy(d32).pin_memory()
@@ -293,6 +300,8 @@ def setup_map(args, dev, rank):
                                                     wl.bins.edges_deg[0], wl.bins.edges_deg[-1]),
               "m_max": M, "pass": "forward + adjoint", "pairs_per_step_per_gpu": total,
               "contraction": "tensor cores, TF32x3" if args.contract == "tc" else "FP32 pipe",
+              "pivots": "all" if piv is None else "profile band: %d rings from z = 1/2 (%d pivots)" % (
+                  args.profile_band, piv[1] - piv[0]),
               "l2": "inputs larger than L2 (%.2f GB of (w d, w) per map)" % (8 * 12 * wl.nside ** 2 / 1e9)
               if 12 * wl.nside ** 2 * 8 > 129e6 else "L2 flushed between steps",
               "parallelism": "independent map per GPU"}
@@ -614,6 +623,9 @@ def main():
     ap.add_argument("--cpu-pivots", type=int, default=2048)
     ap.add_argument("--ref-pivots", type=int, default=512)
     ap.add_argument("--batch-nsides", default="256,512,1024,2048")
+    ap.add_argument("--profile-band", type=int, default=0,
+                    help="map workloads: restrict the pivots to this many belt rings from z = 1/2 "
+                         "(for ncu captures of full-resolution kernels; not a bench configuration)")
     ap.add_argument("--contract", default="fp32", choices=["fp32", "tc"],
                     help="contraction of the map forward: FP32 pipe or tensor cores (TF32x3)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -44,17 +44,15 @@ __device__ __forceinline__ int cat_bin(float c2, const float* sE2, const unsigne
 
 template <int M, bool SELF>
 __device__ __forceinline__ void cat_flush(float* sA, float* sW, float* sQ, float* sQW, int k, int lane,
-                                          float (&re)[M + 1], float (&im)[M + 1], float& W, float& Q, float& QW) {
+                                          float2 (&acc)[M + 1], float& W, float& Q, float& QW) {
     float* a = sA + (size_t)k * (M + 1) * 2 * TILE;
-    atomicAdd(a + lane, re[0]);
-    re[0] = 0.0f;
-    im[0] = 0.0f;
+    atomicAdd(a + lane, acc[0].x);
+    acc[0] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int m = 1; m <= M; ++m) {
-        atomicAdd(a + (2 * m) * TILE + lane, re[m]);
-        atomicAdd(a + (2 * m + 1) * TILE + lane, im[m]);
-        re[m] = 0.0f;
-        im[m] = 0.0f;
+        atomicAdd(a + (2 * m) * TILE + lane, acc[m].x);
+        atomicAdd(a + (2 * m + 1) * TILE + lane, acc[m].y);
+        acc[m] = make_float2(0.0f, 0.0f);
     }
     atomicAdd(sW + k * TILE + lane, W);
     W = 0.0f;
@@ -279,19 +277,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall 
         __syncthreads();
         const CatPivot P = cat_pivot(px, py, pz);
 
-        float re[M + 1], im[M + 1];
+        float2 acc[M + 1];
 #pragma unroll
-        for (int m = 0; m <= M; ++m) {
-            re[m] = 0.0f;
-            im[m] = 0.0f;
-        }
+        for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
         float W = 0.0f, Qs = 0.0f, QW = 0.0f;
         int kcur = -1;
         cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
                  [&](int k, float dx, float dy, float dz, float2 v) {
                      const bool on = k >= 0 && k < K;
                      if (on && k != kcur) {
-                         if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, re, im, W, Qs, QW);
+                         if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
                          kcur = k;
                      }
                      const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
@@ -299,14 +294,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall 
                      const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
                      const float wd = on ? v.x : 0.0f;
                      const float ww = on ? v.y : 0.0f;
-                     harmonics<M>(re, im, N * rinv, E * rinv, wd, wd);
+                     harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
                      W += ww;
                      if (SELF) {
                          Qs = fmaf(wd, wd, Qs);
                          QW = fmaf(ww, ww, QW);
                      }
                  });
-        if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, re, im, W, Qs, QW);
+        if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
         __syncthreads();
         tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
         __syncthreads();

@@ -32,7 +32,7 @@ namespace tpcf {
 
 constexpr float AMBIGUITY = 1.0e-6f;  // > worst fp32 error of the edge position (~1.5e-7 px)
 constexpr float FAST_XMAX = 0.25f;    // |half longitude offset| covered by the polynomial
-constexpr int FLUSH_RINGS = 4;        // rings summed in registers before a shared-memory flush
+constexpr int FLUSH_RINGS = 8;        // rings summed in registers before a shared-memory flush
 
 __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
     long long q = a / b;
@@ -163,60 +163,51 @@ __device__ __forceinline__ void pixel_dir(float fi, float xneg, float uneg, cons
     sph = E * rinv;
 }
 
-// acc_re[m] += wc cos(m phi), acc_im[m] += ws sin(m phi), m = 0..M, by the Chebyshev
-// three-term recurrences with the weights folded in.
+// acc[m] += (wc cos(m phi), ws sin(m phi)), m = 0..M, by the Chebyshev three-term
+// recurrences with the weights folded in.  The cosine and sine chains share the
+// coefficient 2 cos(phi), so each step is one packed two-lane FP32 FMA (f32x2) on the
+// state (u_m, v_m), and the accumulation one packed add.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 template <int M>
-__device__ __forceinline__ void harmonics(float (&re)[M + 1], float (&im)[M + 1], float cph, float sph,
-                                          float wc, float ws) {
-    re[0] += wc;
+__device__ __forceinline__ void harmonics(float2 (&acc)[M + 1], float cph, float sph, float wc, float ws) {
+    acc[0].x += wc;
     if constexpr (M >= 1) {
-        float u0 = wc, u1 = wc * cph;
-        float v0 = 0.0f, v1 = ws * sph;
-        re[1] += u1;
-        im[1] += v1;
+        float2 x0 = make_float2(wc, 0.0f);
+        float2 x1 = make_float2(wc * cph, ws * sph);
+        acc[1] = __fadd2_rn(acc[1], x1);
         const float c2 = cph + cph;
+        const float2 C2 = make_float2(c2, c2);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float u2 = fmaf(c2, u1, -u0);
-            const float v2 = fmaf(c2, v1, -v0);
-            re[m] += u2;
-            im[m] += v2;
-            u0 = u1;
-            u1 = u2;
-            v0 = v1;
-            v1 = v2;
+            const float2 x2 = __ffma2_rn(C2, x1, neg2(x0));
+            acc[m] = __fadd2_rn(acc[m], x2);
+            x0 = x1;
+            x1 = x2;
         }
     }
 }
 
 // The same for two pixels a and b at once (two independent recurrence chains for
-// instruction-level parallelism; the sums are added pairwise).
+// instruction-level parallelism; the pair is added before the accumulation).
 template <int M>
-__device__ __forceinline__ void harmonics2(float (&re)[M + 1], float (&im)[M + 1], float ca, float sa,
-                                           float wca, float wsa, float cb, float sb, float wcb, float wsb) {
-    re[0] += wca + wcb;
+__device__ __forceinline__ void harmonics2(float2 (&acc)[M + 1], float ca, float sa, float wca, float wsa, float cb,
+                                           float sb, float wcb, float wsb) {
+    acc[0].x += wca + wcb;
     if constexpr (M >= 1) {
-        float ua0 = wca, ua1 = wca * ca, va0 = 0.0f, va1 = wsa * sa;
-        float ub0 = wcb, ub1 = wcb * cb, vb0 = 0.0f, vb1 = wsb * sb;
-        re[1] += ua1 + ub1;
-        im[1] += va1 + vb1;
-        const float c2a = ca + ca, c2b = cb + cb;
+        float2 xa0 = make_float2(wca, 0.0f), xa1 = make_float2(wca * ca, wsa * sa);
+        float2 xb0 = make_float2(wcb, 0.0f), xb1 = make_float2(wcb * cb, wsb * sb);
+        acc[1] = __fadd2_rn(acc[1], __fadd2_rn(xa1, xb1));
+        const float2 Ca = make_float2(ca + ca, ca + ca), Cb = make_float2(cb + cb, cb + cb);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float ua2 = fmaf(c2a, ua1, -ua0);
-            const float ub2 = fmaf(c2b, ub1, -ub0);
-            const float va2 = fmaf(c2a, va1, -va0);
-            const float vb2 = fmaf(c2b, vb1, -vb0);
-            re[m] += ua2 + ub2;
-            im[m] += va2 + vb2;
-            ua0 = ua1;
-            ua1 = ua2;
-            ub0 = ub1;
-            ub1 = ub2;
-            va0 = va1;
-            va1 = va2;
-            vb0 = vb1;
-            vb1 = vb2;
+            const float2 xa2 = __ffma2_rn(Ca, xa1, neg2(xa0));
+            const float2 xb2 = __ffma2_rn(Cb, xb1, neg2(xb0));
+            acc[m] = __fadd2_rn(acc[m], __fadd2_rn(xa2, xb2));
+            xa0 = xa1;
+            xa1 = xa2;
+            xb0 = xb1;
+            xb1 = xb2;
         }
     }
 }
@@ -245,8 +236,7 @@ struct DirectLoad {
 // Two pixels per iteration.
 template <int M, bool FAST, bool SELF, class L>
 __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
-                                         float (&re)[M + 1], float (&im)[M + 1], float& W, float& Q,
-                                         float& QW) {
+                                         float2 (&acc)[M + 1], float& W, float& Q, float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
@@ -261,7 +251,7 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
         float ca, sa, cb, sb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        harmonics2<M>(re, im, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x);
+        harmonics2<M>(acc, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x);
         W += v0.y + v1.y;
         if (SELF) {
             Q = fmaf(v0.x, v0.x, fmaf(v1.x, v1.x, Q));
@@ -276,8 +266,8 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
 // (four pixels) per iteration.
 template <int M, bool FAST, bool SELF, class L>
 __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
-                                           int mb, float (&re)[M + 1], float (&im)[M + 1], float& W,
-                                           float& Q, float& QW) {
+                                           int mb, float2 (&acc)[M + 1], float& W, float& Q,
+                                           float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
@@ -296,7 +286,7 @@ __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const 
         float ca, sa, cb, sb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        harmonics2<M>(re, im, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x);
+        harmonics2<M>(acc, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x);
         W += (p0.y + m0.y) + (p1.y + m1.y);
         if (SELF) {
             Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, fmaf(p1.x, p1.x, fmaf(m1.x, m1.x, Q))));
@@ -407,7 +397,7 @@ __device__ __forceinline__ ExactCtx exact_ctx(const MapDev& g, const PivotRing& 
 // Accumulate the bin-k moments of ring r into the lane's registers.
 template <int M, bool SELF, class L>
 __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P, int r, int k, int q,
-                                             const L& ld, float (&re)[M + 1], float (&im)[M + 1], float& W,
+                                             const L& ld, float2 (&acc)[M + 1], float& W,
                                              float& Q, float& QW) {
     const long long pr = P.pair0 + (r - P.rlo);
     const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
@@ -423,7 +413,7 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
             const float2 v = ld(R.first + wrap_idx(c.cint, R.n));
             float cph, sph;
             pixel_dir<false>(0.0f, 0.0f, -c.cfrac * R.inv_n, R, cph, sph);
-            harmonics<M>(re, im, cph, sph, v.x, v.x);
+            harmonics<M>(acc, cph, sph, v.x, v.x);
             W += v.y;
             if (SELF) {
                 Q = fmaf(v.x, v.x, Q);
@@ -432,19 +422,19 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
         }
         const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
         if (fast)
-            walk_pairs<M, true, SELF>(R, ld, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
+            walk_pairs<M, true, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW);
         else
-            walk_pairs<M, false, SELF>(R, ld, c, b.a0, b.n0, b.mb, re, im, W, Q, QW);
+            walk_pairs<M, false, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW);
         return;
     }
     const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
     const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
     if (fast) {
-        walk_run<M, true, SELF>(R, ld, c, b.a0, b.n0, re, im, W, Q, QW);
-        walk_run<M, true, SELF>(R, ld, c, b.a1, b.n1, re, im, W, Q, QW);
+        walk_run<M, true, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW);
+        walk_run<M, true, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW);
     } else {
-        walk_run<M, false, SELF>(R, ld, c, b.a0, b.n0, re, im, W, Q, QW);
-        walk_run<M, false, SELF>(R, ld, c, b.a1, b.n1, re, im, W, Q, QW);
+        walk_run<M, false, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW);
+        walk_run<M, false, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW);
     }
 }
 
@@ -479,27 +469,23 @@ __device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P
     for (int k = 0; k < g.K; ++k) {
         const int2 br = g.bin_range[(long long)P.i * g.K + k];
         if (br.x + warp > br.y) continue;
-        float re[M + 1], im[M + 1];
+        float2 acc[M + 1];
 #pragma unroll
-        for (int m = 0; m <= M; ++m) {
-            re[m] = 0.0f;
-            im[m] = 0.0f;
-        }
+        for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
         float W = 0.0f, Q = 0.0f, QW = 0.0f;
         float* a = sA + (size_t)k * (M + 1) * 2 * TILE;
         // Blocked summation: the registers sum FLUSH_RINGS rings, then the block is
         // added into shared memory, which keeps the running sums short.
         int nr = 0;
         for (int r = br.x + warp; r <= br.y; r += NWARPS) {
-            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, re, im, W, Q, QW);
+            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, acc, W, Q, QW);
             if (++nr == FLUSH_RINGS || r + NWARPS > br.y) {
                 nr = 0;
 #pragma unroll
                 for (int m = 0; m <= M; ++m) {
-                    atomicAdd(a + (2 * m) * TILE + lane, re[m]);
-                    atomicAdd(a + (2 * m + 1) * TILE + lane, im[m]);
-                    re[m] = 0.0f;
-                    im[m] = 0.0f;
+                    atomicAdd(a + (2 * m) * TILE + lane, acc[m].x);
+                    atomicAdd(a + (2 * m + 1) * TILE + lane, acc[m].y);
+                    acc[m] = make_float2(0.0f, 0.0f);
                 }
                 atomicAdd(sW + k * TILE + lane, W);
                 W = 0.0f;
@@ -854,7 +840,7 @@ __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int 
 }
 
 template <int M, bool SELF, bool DIRECT>
-__global__ void __launch_bounds__(NTHREADS, 2) map_fwd_kernel(MapDev g, MapCall c) {
+__global__ void __launch_bounds__(NTHREADS, 3) map_fwd_kernel(MapDev g, MapCall c) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
     double* slot = c.slots + (size_t)blockIdx.x * n_entries(g.K, M);
@@ -980,28 +966,25 @@ __global__ void __launch_bounds__(NTHREADS) map_count_kernel(MapDev g, const flo
 constexpr int ROW = 512;  // floats per warp row buffer (wider rows fall back to whole-ring or global adds)
 
 // val = sum_m (cos(m phi) hr_m + sin(m phi) hi_m): X the cosine part, Y the sine part.
+// h[m] = (hr_m, hi_m); the (cos, sin) chains run packed as in harmonics().
 template <int M>
-__device__ __forceinline__ void adj_harmonics(const float (&hr)[M + 1], const float (&hi)[M + 1], float cph,
-                                              float sph, float& X, float& Y) {
-    X = hr[0];
-    Y = 0.0f;
+__device__ __forceinline__ void adj_harmonics(const float2 (&h)[M + 1], float cph, float sph, float& X, float& Y) {
+    float2 xy = make_float2(h[0].x, 0.0f);
     if constexpr (M >= 1) {
-        float t0 = 1.0f, t1 = cph, s0 = 0.0f, s1 = sph;
-        X = fmaf(t1, hr[1], X);
-        Y = s1 * hi[1];
+        float2 t0 = make_float2(1.0f, 0.0f), t1 = make_float2(cph, sph);
+        xy = __ffma2_rn(t1, h[1], xy);
         const float c2 = cph + cph;
+        const float2 C2 = make_float2(c2, c2);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float t2 = fmaf(c2, t1, -t0);
-            const float s2 = fmaf(c2, s1, -s0);
-            X = fmaf(t2, hr[m], X);
-            Y = fmaf(s2, hi[m], Y);
+            const float2 t2 = __ffma2_rn(C2, t1, neg2(t0));
+            xy = __ffma2_rn(t2, h[m], xy);
             t0 = t1;
             t1 = t2;
-            s0 = s1;
-            s1 = s2;
         }
     }
+    X = xy.x;
+    Y = xy.y;
 }
 
 // Where the contribution to pixel p (unwrapped index on ring R) goes.
@@ -1022,46 +1005,36 @@ __device__ __forceinline__ void sink_add(const RowSink& s, int p_unwrapped, int 
 }
 
 template <int M>
-__device__ __forceinline__ void adj_harmonics2(const float (&hr)[M + 1], const float (&hi)[M + 1], float ca,
-                                               float sa, float cb, float sb, float& Xa, float& Ya, float& Xb,
-                                               float& Yb) {
-    Xa = hr[0];
-    Xb = hr[0];
-    Ya = 0.0f;
-    Yb = 0.0f;
+__device__ __forceinline__ void adj_harmonics2(const float2 (&h)[M + 1], float ca, float sa, float cb, float sb,
+                                               float& Xa, float& Ya, float& Xb, float& Yb) {
+    float2 xya = make_float2(h[0].x, 0.0f), xyb = xya;
     if constexpr (M >= 1) {
-        float ta0 = 1.0f, ta1 = ca, sa0 = 0.0f, sa1 = sa;
-        float tb0 = 1.0f, tb1 = cb, sb0 = 0.0f, sb1 = sb;
-        Xa = fmaf(ta1, hr[1], Xa);
-        Xb = fmaf(tb1, hr[1], Xb);
-        Ya = sa1 * hi[1];
-        Yb = sb1 * hi[1];
-        const float c2a = ca + ca, c2b = cb + cb;
+        float2 ta0 = make_float2(1.0f, 0.0f), ta1 = make_float2(ca, sa);
+        float2 tb0 = ta0, tb1 = make_float2(cb, sb);
+        xya = __ffma2_rn(ta1, h[1], xya);
+        xyb = __ffma2_rn(tb1, h[1], xyb);
+        const float2 Ca = make_float2(ca + ca, ca + ca), Cb = make_float2(cb + cb, cb + cb);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float ta2 = fmaf(c2a, ta1, -ta0);
-            const float tb2 = fmaf(c2b, tb1, -tb0);
-            const float sa2 = fmaf(c2a, sa1, -sa0);
-            const float sb2 = fmaf(c2b, sb1, -sb0);
-            Xa = fmaf(ta2, hr[m], Xa);
-            Xb = fmaf(tb2, hr[m], Xb);
-            Ya = fmaf(sa2, hi[m], Ya);
-            Yb = fmaf(sb2, hi[m], Yb);
+            const float2 ta2 = __ffma2_rn(Ca, ta1, neg2(ta0));
+            const float2 tb2 = __ffma2_rn(Cb, tb1, neg2(tb0));
+            xya = __ffma2_rn(ta2, h[m], xya);
+            xyb = __ffma2_rn(tb2, h[m], xyb);
             ta0 = ta1;
             ta1 = ta2;
             tb0 = tb1;
             tb1 = tb2;
-            sa0 = sa1;
-            sa1 = sa2;
-            sb0 = sb1;
-            sb1 = sb2;
         }
     }
+    Xa = xya.x;
+    Ya = xya.y;
+    Xb = xyb.x;
+    Yb = xyb.y;
 }
 
 template <int M, bool FAST>
 __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
-                                        int a, int len, const float (&hr)[M + 1], const float (&hi)[M + 1],
+                                        int a, int len, const float2 (&h)[M + 1],
                                         float wdi, const RowSink& s) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
@@ -1078,7 +1051,7 @@ __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restri
         float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        adj_harmonics2<M>(hr, hi, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
+        adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
         if (on0) sink_add(s, a + t, idx, wdi * v0.y * (Xa + Ya));
         if (on1) sink_add(s, a + t + 1, idx1, wdi * v1.y * (Xb + Yb));
         idx = idx1 + 1 >= R.n ? idx1 + 1 - R.n : idx1 + 1;
@@ -1087,8 +1060,8 @@ __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restri
 
 template <int M, bool FAST>
 __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
-                                          int a, int len, int mb, const float (&hr)[M + 1],
-                                          const float (&hi)[M + 1], float wdi, const RowSink& s) {
+                                          int a, int len, int mb, const float2 (&h)[M + 1], float wdi,
+                                          const RowSink& s) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
@@ -1108,7 +1081,7 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
         float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        adj_harmonics2<M>(hr, hi, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
+        adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
         if (on0) {
             sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya));
             sink_add(s, mb - a - t, im_, wdi * m0.y * (Xa - Ya));
@@ -1170,12 +1143,11 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
         const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
         const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
         if (Tk.x == T_INF || Tk1.x == T_ZERO) continue;
-        float hr[M + 1], hi[M + 1];
+        float2 h[M + 1];
         const float* hk = sH + (size_t)k * (M + 1) * 2 * TILE;
 #pragma unroll
         for (int m = 0; m <= M; ++m) {
-            hr[m] = hk[(2 * m) * TILE + lane];
-            hi[m] = hk[(2 * m + 1) * TILE + lane];
+            h[m] = make_float2(hk[(2 * m) * TILE + lane], hk[(2 * m + 1) * TILE + lane]);
         }
         const bool sym = (R.n == P.n_i) && (Tk1.x != T_INF);
         const BinRuns b = bin_runs(c, Tk, Tk1, g.E[k], g.E[k + 1], x, R.n, sym);
@@ -1186,23 +1158,23 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
                 const float2 v = __ldg(wdw + R.first + pw);
                 float cph, sph, X, Y;
                 pixel_dir<false>(0.0f, 0.0f, -c.cfrac * R.inv_n, R, cph, sph);
-                adj_harmonics<M>(hr, hi, cph, sph, X, Y);
+                adj_harmonics<M>(h, cph, sph, X, Y);
                 sink_add(s, p, pw, wdi * v.y * (X + Y));
             }
             const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
             if (fast)
-                adj_pairs<M, true>(R, wdw, c, b.a0, b.n0, b.mb, hr, hi, wdi, s);
+                adj_pairs<M, true>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s);
             else
-                adj_pairs<M, false>(R, wdw, c, b.a0, b.n0, b.mb, hr, hi, wdi, s);
+                adj_pairs<M, false>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s);
         } else {
             const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
             const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
             if (fast) {
-                adj_run<M, true>(R, wdw, c, b.a0, b.n0, hr, hi, wdi, s);
-                adj_run<M, true>(R, wdw, c, b.a1, b.n1, hr, hi, wdi, s);
+                adj_run<M, true>(R, wdw, c, b.a0, b.n0, h, wdi, s);
+                adj_run<M, true>(R, wdw, c, b.a1, b.n1, h, wdi, s);
             } else {
-                adj_run<M, false>(R, wdw, c, b.a0, b.n0, hr, hi, wdi, s);
-                adj_run<M, false>(R, wdw, c, b.a1, b.n1, hr, hi, wdi, s);
+                adj_run<M, false>(R, wdw, c, b.a0, b.n0, h, wdi, s);
+                adj_run<M, false>(R, wdw, c, b.a1, b.n1, h, wdi, s);
             }
         }
     }
@@ -1219,10 +1191,15 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
     }
 }
 
+// Shared memory of an adjoint tile: phases 1-2 use the moments A, W, Q, QW, the
+// pivot values, the primary-term sums and one m of H; phase 3 keeps only A (now h)
+// and puts the warps' row buffers where W and the rest were.
 template <int M>
 __host__ __device__ inline size_t bwd_tile_floats(int K) {
-    return (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE + 2 * TILE + TILE +
-           (size_t)K * K * 2 + (size_t)NWARPS * ROW;
+    const size_t a = (size_t)K * (M + 1) * 2 * TILE;
+    const size_t p12 = a + 3 * (size_t)K * TILE + 2 * TILE + TILE + (size_t)K * K * 2;
+    const size_t p3 = a + (size_t)NWARPS * ROW;
+    return p12 > p3 ? p12 : p3;
 }
 
 // One adjoint tile (all three phases).  Called by every thread of the CTA.
@@ -1236,7 +1213,7 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
     float* sPiv = sQW + K * TILE;
     float* sPrim = sPiv + 2 * TILE;
     float* sHm = sPrim + TILE;                  // [K][K][2] one m at a time
-    float* sRow = sHm + (size_t)K * K * 2;      // [NWARPS][ROW]
+    float* sRow = sW;                           // [NWARPS][ROW], phase 3 only
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t nfl = (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE;
 
@@ -1300,6 +1277,7 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
         const float gp = 0.5f * pv.y * sPrim[lane];
         if (gp != 0.0f) atomicAdd(c.grad + pix, gp);
     }
+    __syncthreads();  // the row buffers of phase 3 overlay sPrim and the rest
     // phase 3: neighbour legs, warps split the neighbour rings
     const int2 rr = g.ring_range[P.i];
     for (int r = rr.x + warp; r <= rr.y; r += NWARPS)
@@ -1308,7 +1286,7 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
 }
 
 template <int M>
-__global__ void __launch_bounds__(NTHREADS, 2) map_bwd_kernel(MapDev g, MapCall c) {
+__global__ void __launch_bounds__(NTHREADS, 3) map_bwd_kernel(MapDev g, MapCall c) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
     for (;;) {
