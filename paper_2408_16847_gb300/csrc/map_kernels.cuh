@@ -222,6 +222,12 @@ __device__ __forceinline__ int wrap_idx(int p, int n) {
 struct PackedLoad {
     const float2* __restrict__ p;
     __device__ __forceinline__ float2 operator()(long long i) const { return __ldg(p + i); }
+    // accessor of one ring's pixels (index relative to the ring's first pixel)
+    struct Row {
+        const float2* __restrict__ p;
+        __device__ __forceinline__ float2 operator()(int i) const { return __ldg(p + i); }
+    };
+    __device__ __forceinline__ Row row(long long first) const { return Row{p + first}; }
 };
 struct DirectLoad {
     const float* __restrict__ d;
@@ -230,22 +236,54 @@ struct DirectLoad {
         const float wi = __ldg(w + i);
         return make_float2(wi * __ldg(d + i), wi);
     }
+    struct Row {
+        const float* __restrict__ d;
+        const float* __restrict__ w;
+        __device__ __forceinline__ float2 operator()(int i) const {
+            const float wi = __ldg(w + i);
+            return make_float2(wi * __ldg(d + i), wi);
+        }
+    };
+    __device__ __forceinline__ Row row(long long first) const { return Row{d + first, w + first}; }
 };
 
 // Walk pixels [a, a + len) of ring R (lane-private run), accumulating into the bin.
-// Two pixels per iteration.
+// Two pixels per iteration.  When no lane's run wraps around the ring, the first
+// min-length iterations run without predicates or index wrapping; the rest (and
+// wrapping runs) take the general loop.
 template <int M, bool FAST, bool SELF, class L>
 __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
                                          float2 (&acc)[M + 1], float& W, float& Q, float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    if (maxlen <= 0) return;
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
     int idx = wrap_idx(a, R.n);
-    for (int t = 0; t < maxlen; t += 2) {
+    const auto row = ld.row(R.first);
+    int t = 0;
+    const int minlen = __reduce_min_sync(0xffffffffu, len);
+    if (minlen >= 2 && __all_sync(0xffffffffu, idx + len <= R.n)) {
+        float ft = i0;
+        for (; t + 1 < minlen; t += 2, ft += 2.0f) {
+            const float2 v0 = row(idx + t), v1 = row(idx + t + 1);
+            float ca, sa, cb, sb;
+            pixel_dir<FAST>(ft, xneg, uneg, R, ca, sa);
+            pixel_dir<FAST>(ft + 1.0f, xneg, uneg, R, cb, sb);
+            harmonics2<M>(acc, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x);
+            W += v0.y + v1.y;
+            if (SELF) {
+                Q = fmaf(v0.x, v0.x, fmaf(v1.x, v1.x, Q));
+                QW = fmaf(v0.y, v0.y, fmaf(v1.y, v1.y, QW));
+            }
+        }
+        idx += t;
+        if (idx >= R.n) idx -= R.n;
+    }
+    for (; t < maxlen; t += 2) {
         const bool on0 = t < len, on1 = t + 1 < len;
         const int idx1 = idx + 1 >= R.n ? idx + 1 - R.n : idx + 1;
-        const float2 v0 = on0 ? ld(R.first + idx) : make_float2(0.0f, 0.0f);
-        const float2 v1 = on1 ? ld(R.first + idx1) : make_float2(0.0f, 0.0f);
+        const float2 v0 = on0 ? row(idx) : make_float2(0.0f, 0.0f);
+        const float2 v1 = on1 ? row(idx1) : make_float2(0.0f, 0.0f);
         const float oa = on0 ? i0 + (float)t : i0;
         const float ob = on1 ? i0 + (float)(t + 1) : i0;
         float ca, sa, cb, sb;
@@ -263,24 +301,48 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
 
 // Walk the pixel pairs (p, mb - p), p in [a, a + len): mirror images about the
 // pivot's meridian (belt rings with as many pixels as the pivot ring).  Two pairs
-// (four pixels) per iteration.
+// (four pixels) per iteration; the same no-wrap fast loop as walk_run.
 template <int M, bool FAST, bool SELF, class L>
 __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
                                            int mb, float2 (&acc)[M + 1], float& W, float& Q,
                                            float& QW) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    if (maxlen <= 0) return;
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
     int ip = wrap_idx(a, R.n);
     int im_ = wrap_idx(mb - a, R.n);
-    for (int t = 0; t < maxlen; t += 2) {
+    const auto row = ld.row(R.first);
+    int t = 0;
+    const int minlen = __reduce_min_sync(0xffffffffu, len);
+    if (minlen >= 2 && __all_sync(0xffffffffu, ip + len <= R.n && im_ - len + 1 >= 0)) {
+        float ft = i0;
+        for (; t + 1 < minlen; t += 2, ft += 2.0f) {
+            const float2 p0 = row(ip + t), m0 = row(im_ - t);
+            const float2 p1 = row(ip + t + 1), m1 = row(im_ - t - 1);
+            float ca, sa, cb, sb;
+            pixel_dir<FAST>(ft, xneg, uneg, R, ca, sa);
+            pixel_dir<FAST>(ft + 1.0f, xneg, uneg, R, cb, sb);
+            harmonics2<M>(acc, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x);
+            W += (p0.y + m0.y) + (p1.y + m1.y);
+            if (SELF) {
+                Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, fmaf(p1.x, p1.x, fmaf(m1.x, m1.x, Q))));
+                QW = fmaf(p0.y, p0.y, fmaf(m0.y, m0.y, fmaf(p1.y, p1.y, fmaf(m1.y, m1.y, QW))));
+            }
+        }
+        ip += t;
+        if (ip >= R.n) ip -= R.n;
+        im_ -= t;
+        if (im_ < 0) im_ += R.n;
+    }
+    for (; t < maxlen; t += 2) {
         const bool on0 = t < len, on1 = t + 1 < len;
         const int ip1 = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
         const int im1 = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
-        const float2 p0 = on0 ? ld(R.first + ip) : make_float2(0.0f, 0.0f);
-        const float2 m0 = on0 ? ld(R.first + im_) : make_float2(0.0f, 0.0f);
-        const float2 p1 = on1 ? ld(R.first + ip1) : make_float2(0.0f, 0.0f);
-        const float2 m1 = on1 ? ld(R.first + im1) : make_float2(0.0f, 0.0f);
+        const float2 p0 = on0 ? row(ip) : make_float2(0.0f, 0.0f);
+        const float2 m0 = on0 ? row(im_) : make_float2(0.0f, 0.0f);
+        const float2 p1 = on1 ? row(ip1) : make_float2(0.0f, 0.0f);
+        const float2 m1 = on1 ? row(im1) : make_float2(0.0f, 0.0f);
         const float oa = on0 ? i0 + (float)t : i0;
         const float ob = on1 ? i0 + (float)(t + 1) : i0;
         float ca, sa, cb, sb;
