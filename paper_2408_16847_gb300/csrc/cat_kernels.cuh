@@ -226,7 +226,7 @@ __device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restri
 }
 
 template <int M, bool SELF>
-__global__ void __launch_bounds__(NTHREADS, 2) cat_fwd_kernel(CatDev g, MapCall c) {
+__global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall c) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_tile;
     __shared__ double s_cap[4];  // centre (x, y, z), query radius
