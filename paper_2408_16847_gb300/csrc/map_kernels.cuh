@@ -594,8 +594,8 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
                 sr = fmaf(wd[l], fmaf(a, cc, b * d), sr);
                 si = fmaf(wd[l], fmaf(a, d, -b * cc), si);
             }
-            slot[2 * e] += (double)sr;
-            slot[2 * e + 1] += (double)si;
+            atomicAdd(slot + 2 * e, (double)sr);  // no return value: a reduction, no wait
+            atomicAdd(slot + 2 * e + 1, (double)si);
         } else if (e < nS + P) {
             const int pidx = e - nS;
             int k2 = (int)((sqrtf(8.0f * pidx + 1.0f) - 1.0f) * 0.5f);
@@ -608,7 +608,7 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
                 const int l = (j + threadIdx.x) & (TILE - 1);
                 s = fmaf(wt[l], sW[k1 * TILE + l] * sW[k2 * TILE + l], s);
             }
-            slot[nS + e] += (double)s;
+            atomicAdd(slot + nS + e, (double)s);
         } else {
             const int k = e - nS - P;
             float s1 = 0.0f, s2 = 0.0f;
@@ -617,8 +617,8 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
                 s1 = fmaf(wd[l], sQ[k * TILE + l], s1);
                 s2 = fmaf(wt[l], sQW[k * TILE + l], s2);
             }
-            slot[2 * nS + P + k] += (double)s1;
-            slot[2 * nS + P + K + k] += (double)s2;
+            atomicAdd(slot + 2 * nS + P + k, (double)s1);
+            atomicAdd(slot + 2 * nS + P + K + k, (double)s2);
         }
     }
 }
@@ -814,7 +814,7 @@ __device__ void tile_contract_tc(int K, const float* sA, const float* sW, const 
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int k2 = c0 + j;
-                            if (k2 >= r && k2 < K) slot[2 * nS + k2 * (k2 + 1) / 2 + r] += (double)v[j];
+                            if (k2 >= r && k2 < K) atomicAdd(slot + 2 * nS + k2 * (k2 + 1) / 2 + r, (double)v[j]);
                         }
                     }
                 } else {
@@ -828,8 +828,8 @@ __device__ void tile_contract_tc(int K, const float* sA, const float* sW, const 
                             const int k2 = (c0 >> 1) + j;
                             if (k2 >= k1 && k2 < K) {
                                 const int e = mm * P + k2 * (k2 + 1) / 2 + k1;
-                                slot[2 * e] += (double)(v[2 * j] + u[2 * j + 1]);
-                                slot[2 * e + 1] += (double)(v[2 * j + 1] - u[2 * j]);
+                                atomicAdd(slot + 2 * e, (double)(v[2 * j] + u[2 * j + 1]));
+                                atomicAdd(slot + 2 * e + 1, (double)(v[2 * j + 1] - u[2 * j]));
                             }
                         }
                     }
@@ -848,8 +848,8 @@ __device__ void tile_contract_tc(int K, const float* sA, const float* sW, const 
                 s1 = fmaf(wd[j], sQ[k * TILE + j], s1);
                 s2 = fmaf(wt[j], sQW[k * TILE + j], s2);
             }
-            slot[2 * nS + P + k] += (double)s1;
-            slot[2 * nS + P + K + k] += (double)s2;
+            atomicAdd(slot + 2 * nS + P + k, (double)s1);
+            atomicAdd(slot + 2 * nS + P + K + k, (double)s2);
         }
     }
 }
@@ -983,6 +983,7 @@ __global__ void __launch_bounds__(NTHREADS) map_count_kernel(MapDev g, const flo
         const long long pix = g.ring_first[P.i] + q;
         const bool in = (q < P.n_i) && pix >= piv_lo && pix < piv_hi;
         const bool live = in && wdw[pix].y != 0.0f;
+        if (!__syncthreads_or(live)) continue;
         const int qg = min(q, P.n_i - 1);
         unsigned long long n_sym = 0, n_plain = 0;
         for (int k = 0; k < g.K; ++k) {
