@@ -122,7 +122,7 @@ def cat_flops_per_pair(M: int):
 # DRAM bytes per pixel per launch of the map kernels, from the ncu capture of the
 # Nside 512 case (profiles/map_kernels_fullsky_nside512.md: dram__bytes_read.sum +
 # dram__bytes_write.sum / pixels), valid only for the kernel source it was taken on.
-TRAFFIC = {"map_bwd_kernel": (18.25, "0f0c9681da815ec7"), "map_fwd_kernel": (19.71, "0f0c9681da815ec7")}
+TRAFFIC = {"map_bwd_kernel": (18.24, "aef844b129b8dbdc"), "map_fwd_kernel": (19.26, "aef844b129b8dbdc")}
 
 
 def traffic_per_launch(kernel, npix):
