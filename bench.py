@@ -42,7 +42,12 @@ sys.path.insert(0, ROOT)
 METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
-MAP_WORKLOADS = ("fullsky_nside4096", "masked_map_nside1024", "fullsky_nside512", "map_nside64")
+MAP_WORKLOADS = ("fullsky_nside4096", "masked_map_nside1024", "fullsky_nside512", "map_nside64",
+                 "fullsky_nside4096_paper")
+# The paper's exact-path timing (Sec. 4): ~40 min for one Nside 4096 map, 20 log bins over
+# 8-200 arcmin, m <= 8, forward only, one 128-thread CPU node; with the 3.42e13 in-bin
+# pairs of that shape (N^2 (cos 8' - cos 200') / 2) that is 1.43e10 pairs/s.
+PAPER_FWD_PAIRS_PER_S = {"fullsky_nside4096_paper": 3.42e13 / 2400.0}
 
 
 def log(*a):
@@ -185,7 +190,7 @@ class ClockSampler:
 
 # -------------------------------------------------------------- CPU baseline
 
-def oracle_sample(wl, d32, w32, n_piv: int):
+def oracle_sample(wl, d32, w32, n_piv: int, adjoint: bool = True):
     """The FP64 oracle, as it stands, on a bounded sample of a map workload: n_piv
     consecutive pivots on the belt ring at z = 1/2 (outside the galactic mask),
     neighbours from every pixel within the outer bin edge.
@@ -212,7 +217,8 @@ def oracle_sample(wl, d32, w32, n_piv: int):
     t0 = time.perf_counter()
     ref = oracle.zeta(xyz, d, w, wl.bins.edges_deg, M, pivots=piv)
     t1 = time.perf_counter()
-    oracle.gradient(xyz, d, w, wl.bins.edges_deg, M, cot.astype(np.complex128), pivots=piv, targets=piv)
+    if adjoint:
+        oracle.gradient(xyz, d, w, wl.bins.edges_deg, M, cot.astype(np.complex128), pivots=piv, targets=piv)
     t2 = time.perf_counter()
     return dict(t_fwd=t1 - t0, t_bwd=t2 - t1, pairs=ref["pairs"], lo=lo, hi=hi, zeta=ref["zeta"],
                 cores=int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), npts=len(idx),
@@ -263,11 +269,14 @@ def setup_map(args, dev, rank):
     total, n_sym, n_single = plan.count_pairs(w_dev, piv)
     state = {}
 
+    fwd_only = args.pass_ == "forward"
+
     def step(ev=None):
         zeta, norm = plan.forward(d_dev, w_dev, piv)
         if ev is not None:
             ev.record(torch.cuda.current_stream())
-        state["grad"] = plan.backward(d_dev, w_dev, norm, g_dev, piv)
+        if not fwd_only:
+            state["grad"] = plan.backward(d_dev, w_dev, norm, g_dev, piv)
 
     # e2e: the public host-buffer call, with its copies inside the timed region
     h_d = torch.from_numpy(d32).pin_memory()
@@ -278,7 +287,10 @@ def setup_map(args, dev, rank):
     h_g = torch.empty(plan.npoints, dtype=torch.float32).pin_memory()
 
     def e2e_step():
-        plan.run_host_into(h_d, h_w, h_dl, out=(h_z, h_n, h_g))
+        if fwd_only:
+            plan.run_host_into(h_d, h_w, None, out=(h_z, h_n, None))
+        else:
+            plan.run_host_into(h_d, h_w, h_dl, out=(h_z, h_n, h_g))
 
     f_single, f_mirror = flops_per_pair(M, adjoint=False)
     a_single, a_mirror = flops_per_pair(M, adjoint=True)
@@ -286,7 +298,7 @@ def setup_map(args, dev, rank):
     adj_flops = n_single * a_single + n_sym * a_mirror
 
     def cpu_baseline(n_piv):
-        s = oracle_sample(wl, d32, w32, n_piv)
+        s = oracle_sample(wl, d32, w32, n_piv, adjoint=not fwd_only)
         zs, _ = plan.forward(d_dev, w_dev, (s["lo"], s["hi"]))
         zg = tpcf.as_complex(zs).cpu().numpy()
         zo = s["zeta"]
@@ -298,18 +310,24 @@ def setup_map(args, dev, rank):
     config = {"workload": wl.name, "nside": wl.nside, "npix": 12 * wl.nside * wl.nside,
               "bins": "%d %s bins %.2f-%.2f deg" % (K, "lin" if wl.name == "map_nside64" else "log",
                                                     wl.bins.edges_deg[0], wl.bins.edges_deg[-1]),
-              "m_max": M, "pass": "forward + adjoint", "pairs_per_step_per_gpu": total,
+              "m_max": M, "pass": "forward" if fwd_only else "forward + adjoint", "pairs_per_step_per_gpu": total,
               "contraction": "tensor cores, TF32x3" if args.contract == "tc" else "FP32 pipe",
               "pivots": "all" if piv is None else "profile band: %d rings from z = 1/2 (%d pivots)" % (
                   args.profile_band, piv[1] - piv[0]),
               "l2": "inputs larger than L2 (%.2f GB of (w d, w) per map)" % (8 * 12 * wl.nside ** 2 / 1e9)
               if 12 * wl.nside ** 2 * 8 > 129e6 else "L2 flushed between steps",
               "parallelism": "independent map per GPU"}
-    return dict(step=step, split=("forward", "adjoint"), pairs=total, e2e=e2e_step,
-                e2e_bytes=(h_d.numel() * 4 + h_w.numel() * 4 + h_dl.numel() * 8,
-                           h_z.numel() * 8 + h_n.numel() * 8 + h_g.numel() * 4),
+    return dict(step=step, split=("forward", None if fwd_only else "adjoint"), pairs=total, e2e=e2e_step,
+                e2e_bytes=(h_d.numel() * 4 + h_w.numel() * 4 + (0 if fwd_only else h_dl.numel() * 8),
+                           h_z.numel() * 8 + h_n.numel() * 8 + (0 if fwd_only else h_g.numel() * 4)),
+                vs_baseline=PAPER_FWD_PAIRS_PER_S.get(wl.name) if (fwd_only and not args.profile_band) else None,
                 launches=plan.kernel_launches, config=config, cpu_baseline=cpu_baseline,
                 roofline=lambda t1, t2, clk: {
+                    "bound": "alu", "kernel": "map_fwd_kernel",
+                    "achieved": fwd_flops / (t1 * 1e-3) / 1e12, "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s",
+                    "traffic": traffic_per_launch("map_fwd_kernel", 12 * wl.nside ** 2),
+                    "traffic_note": "DRAM bytes per launch scaled by pixels from the Nside 512 ncu capture"}
+                if fwd_only else {
                     "bound": "alu", "kernel": "map_bwd_kernel",
                     "achieved": (fwd_flops + adj_flops) / (t2 * 1e-3) / 1e12,  # adjoint recomputes the forward
                     "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s",
@@ -558,7 +576,7 @@ def run_gpu(args):
             "ms_per_step": ms_step,
             "higher_is_better": True,
             "scaling": "weak",
-            "vs_baseline": None,
+            "vs_baseline": (value / W["vs_baseline"]) if W.get("vs_baseline") else None,
             "dtype": "f32",
             "data": "synthetic",
             "config": W["config"],
@@ -626,6 +644,8 @@ def main():
     ap.add_argument("--profile-band", type=int, default=0,
                     help="map workloads: restrict the pivots to this many belt rings from z = 1/2 "
                          "(for ncu captures of full-resolution kernels; not a bench configuration)")
+    ap.add_argument("--pass", dest="pass_", default="both", choices=["both", "forward"],
+                    help="map workloads: forward + adjoint (default) or the forward alone")
     ap.add_argument("--contract", default="fp32", choices=["fp32", "tc"],
                     help="contraction of the map forward: FP32 pipe or tensor cores (TF32x3)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
