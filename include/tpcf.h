@@ -52,7 +52,7 @@ typedef enum {
     TPCF_ERR_CUDA = 2,        /* a CUDA runtime call failed (message: tpcf_last_error) */
     TPCF_ERR_OOM = 3,         /* device allocation failed; nothing leaked           */
     TPCF_ERR_TIMEOUT = 4,     /* a bounded device wait gave up                      */
-    TPCF_ERR_UNSUPPORTED = 5, /* valid request this build does not implement        */
+    TPCF_ERR_UNSUPPORTED = 5, /* valid request the library does not implement      */
     TPCF_ERR_DEVICE = 6       /* a kernel latched an error (bad table / index)      */
 } tpcf_status;
 
