@@ -80,10 +80,10 @@ def map_inputs(wl, rank: int):
     return np.ascontiguousarray(d, np.float32), wl.weights().astype(np.float32)
 
 
-def catalog_inputs(rank: int):
+def catalog_inputs(rank: int, name: str = "catalog_2e7"):
     """Union (data then randoms) positions, delta, w; randoms positions; alpha."""
     import synth
-    wl = synth.catalog_2e7()
+    wl = getattr(synth, name)()
     xd, wd = wl.data()
     xr = wl.randoms()
     if rank > 0:  # an independent draw per rank
@@ -231,7 +231,8 @@ def oracle_sample_catalog(xu, du, wu, edges, M, n_piv: int):
     (data part) and the oracle's raw sums for those pivots."""
     import oracle
     nd = int(np.sum(du > 0))
-    lo, hi = 1_000_000, 1_000_000 + n_piv
+    lo = min(1_000_000, nd // 2)
+    hi = lo + n_piv
     t0 = time.perf_counter()
     ref = oracle.zeta(xu, du.astype(np.float64), wu.astype(np.float64), edges, M, pivots=np.arange(lo, hi))
     t1 = time.perf_counter()
@@ -342,7 +343,7 @@ def setup_catalog(args, dev, rank):
     from paper_2408_16847_gb300 import tpcf
 
     t0 = time.time()
-    wl, xu, du, wu, xr, alpha32 = catalog_inputs(rank)
+    wl, xu, du, wu, xr, alpha32 = catalog_inputs(rank, args.workload)
     log("[rank %d] catalogue ready in %.1fs (%d + %d points)" % (rank, time.time() - t0, len(xu) - len(xr), len(xr)))
     K, M = wl.bins.nbins, wl.bins.m_max
     edges = wl.bins.edges_deg
@@ -481,7 +482,7 @@ def run_gpu(args):
 
     if args.workload in MAP_WORKLOADS:
         W = setup_map(args, dev, rank)
-    elif args.workload == "catalog_2e7":
+    elif args.workload in ("catalog_2e7", "catalog_2e6"):
         W = setup_catalog(args, dev, rank)
     elif args.workload == "batched_maps":
         W = setup_batch(args, dev, rank)
@@ -607,8 +608,8 @@ def run_reference(args):
         sample = lambda: oracle_sample(wl, d32, w32, args.ref_pivots)
         cfg = {"workload": wl.name, "nside": wl.nside, "m_max": wl.bins.m_max, "pass": "forward + adjoint",
                "sample_pivots": args.ref_pivots}
-    elif args.workload == "catalog_2e7":
-        wl, xu, du, wu, xr, _ = catalog_inputs(0)
+    elif args.workload in ("catalog_2e7", "catalog_2e6"):
+        wl, xu, du, wu, xr, _ = catalog_inputs(0, args.workload)
         sample = lambda: oracle_sample_catalog(xu, du, wu, wl.bins.edges_deg, wl.bins.m_max, args.ref_pivots)
         cfg = {"workload": wl.name, "m_max": wl.bins.m_max, "pass": "D-R forward", "sample_pivots": args.ref_pivots}
     else:

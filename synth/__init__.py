@@ -265,6 +265,12 @@ class CatalogWorkload:
         return uniform_sphere(self.n_randoms, rng(self.seed + 23))
 
 
+def catalog_2e6() -> CatalogWorkload:
+    """The catalogue recipe at a tenth of the size (2e6 clustered points, 1e4 parents,
+    6e6 randoms): the case profiled in place of catalog_2e7."""
+    return CatalogWorkload("catalog_2e6", 2_000_000, 10_000, 0.3, 6_000_000, lin_bins(0.1, 2.0, 16, 10))
+
+
 def catalog_2e7() -> CatalogWorkload:
     """2e7 clustered points (1e5 parents, 0.3 deg offsets), 6e7 randoms, 16 lin bins 0.1-2 deg, m<=10."""
     return CatalogWorkload("catalog_2e7", 20_000_000, 100_000, 0.3, 60_000_000,
