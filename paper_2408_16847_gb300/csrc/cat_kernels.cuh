@@ -4,9 +4,10 @@
 // A tile is 32 consecutive points of the grid order (spatially compact), one pivot
 // per lane.  Warp 0 bounds the tile's live pivots by a cap (centre, radius R); every
 // point within R + theta_max of the centre lies in the cells the cap overlaps, which
-// are a handful of contiguous index ranges per colatitude band.  The CTA's warps take
-// the bands round-robin, stage 32 candidates at a time in shared memory and let each
-// lane pair its pivot with all 32.  Per pair: the chord from fp32 hi/lo positions,
+// are a handful of contiguous index ranges per colatitude band.  Every warp walks the
+// bands in reach and takes every 8th chunk of 32 candidates (so the warps finish
+// together), stages the chunk in shared memory and lets each lane pair its pivot with
+// all 32.  Per pair: the chord from fp32 hi/lo positions,
 // the bin from a log-scale lookup table (FP64 check within CAT_AMB of an edge), the
 // position angle from the pivot's local north/east basis, the harmonics by the
 // Chebyshev recurrences.  The per-lane register sums follow one bin at a time and
@@ -90,18 +91,20 @@ __device__ __forceinline__ CatPivot cat_pivot(double px, double py, double pz) {
     P.lx = (float)(px - (double)P.hx);
     P.ly = (float)(py - (double)P.hy);
     P.lz = (float)(pz - (double)P.hz);
-    const double s2 = px * px + py * py;
-    if (s2 > 1e-24) {
-        const double is = 1.0 / sqrt(s2);
-        P.ex = (float)(-py * is);  // east = z x n / |z x n|
-        P.ey = (float)(px * is);
-        P.nx = (float)(-pz * px * is);  // north = n x east
-        P.ny = (float)(-pz * py * is);
-        P.nz = (float)(s2 * is);
+    // the basis in fp32 (its rounding is a fixed rotation of the pivot's frame, which
+    // cancels in a conj(a), plus ~1e-7 of non-orthogonality)
+    const float s2 = fmaf(P.hx, P.hx, P.hy * P.hy);
+    if (s2 > 1e-12f) {
+        const float is = rsqrtf(s2);
+        P.ex = -P.hy * is;  // east = z x n / |z x n|
+        P.ey = P.hx * is;
+        P.nx = -P.hz * P.hx * is;  // north = n x east
+        P.ny = -P.hz * P.hy * is;
+        P.nz = s2 * is;
     } else {  // on the axis: any tangent basis of the same handedness
         P.ex = 0.0f;
         P.ey = 1.0f;
-        P.nx = (float)(-pz);
+        P.nx = -P.hz;
         P.ny = 0.0f;
         P.nz = 0.0f;
     }
@@ -136,10 +139,28 @@ __device__ __forceinline__ void cat_tile_cap(const CatDev& g, bool live, double 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
     if ((threadIdx.x & 31) == 0) {
-        s_cap[0] = cx;
-        s_cap[1] = cy;
-        s_cap[2] = cz;
-        s_cap[3] = r + g.theta_max + CAT_EPS;
+        // bands within reach and the cap's longitude half-width, valid for every
+        // colatitude it reaches; s_cap = (phi_c, dphi, b0, b1, full)
+        const double Q = r + g.theta_max + CAT_EPS;
+        const double thc = atan2(sqrt(cx * cx + cy * cy), cz);
+        double phc = atan2(cy, cx);
+        if (phc < 0.0) phc += 2.0 * M_PI;
+        int b0 = 0, b1 = g.nbands - 1;
+        double full = 1.0, dphi = M_PI;
+        if (Q < M_PI) {
+            b0 = max(0, (int)floor((thc - Q) / g.hband));
+            b1 = min(g.nbands - 1, (int)floor((thc + Q) / g.hband));
+            const double sq = sin(Q), st = sin(thc);
+            if (thc - Q > 0.0 && thc + Q < M_PI && sq < st) {
+                full = 0.0;
+                dphi = asin(sq / st) + CAT_EPS;
+            }
+        }
+        s_cap[0] = phc;
+        s_cap[1] = dphi;
+        s_cap[2] = (double)b0;
+        s_cap[3] = (double)b1;
+        s_cap[4] = full;
     }
 }
 
@@ -153,32 +174,22 @@ __device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restri
                                          float4* wh, float4* wl, float2* wv, F&& f) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = g.K;
-    const double cx = s_cap[0], cy = s_cap[1], cz = s_cap[2], Q = s_cap[3];
-    const double thc = atan2(sqrt(cx * cx + cy * cy), cz);
-    double phc = atan2(cy, cx);
-    if (phc < 0.0) phc += 2.0 * M_PI;
-    int b0 = 0, b1 = g.nbands - 1;
-    bool full = true;
-    double dphi = M_PI;
-    if (Q < M_PI) {
-        b0 = max(0, (int)floor((thc - Q) / g.hband));
-        b1 = min(g.nbands - 1, (int)floor((thc + Q) / g.hband));
-        // longitude half-width of the cap, valid for every colatitude it reaches
-        const double sq = sin(Q), st = sin(thc);
-        if (thc - Q > 0.0 && thc + Q < M_PI && sq < st) {
-            full = false;
-            dphi = asin(sq / st) + CAT_EPS;
-        }
-    }
-    for (int b = b0 + warp; b <= b1; b += NWARPS) {
+    // sector bounds in fp32: the extra 4e-6 rad covers its rounding (phi < 2 pi), so the
+    // cell ranges stay a superset of the cap
+    const float phc = (float)s_cap[0], dphi = (float)s_cap[1] + 4.0e-6f;
+    const int b0 = (int)s_cap[2], b1 = (int)s_cap[3];
+    const bool full = s_cap[4] != 0.0;
+    // every warp walks every band and takes every NWARPS-th chunk of 32 candidates
+    int chunk = 0;
+    for (int b = b0; b <= b1; ++b) {
         const int64_t ns = g.band_ns[b];
         const int64_t cf = g.band_first[b];
         // at most two cell ranges (the sector range may wrap around phi = 0)
         int64_t ca0 = cf, ca1 = cf + ns, cb0 = 0, cb1 = 0;
         if (!full) {
-            const double scale = (double)ns / (2.0 * M_PI);
-            const int64_t sa = (int64_t)floor((phc - dphi) * scale);
-            const int64_t sb = (int64_t)floor((phc + dphi) * scale);
+            const float scale = (float)ns * (float)(0.5 / M_PI);
+            const int64_t sa = (int64_t)floorf((phc - dphi) * scale);
+            const int64_t sb = (int64_t)floorf((phc + dphi) * scale);
             const int64_t len = sb - sa + 1;
             if (len < ns) {
                 int64_t s0 = sa % ns;
@@ -198,7 +209,8 @@ __device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restri
             const int64_t cl0 = sg == 0 ? ca0 : cb0, cl1 = sg == 0 ? ca1 : cb1;
             if (cl1 <= cl0) continue;
             const int64_t p0 = g.cell_start[cl0], p1 = g.cell_start[cl1];
-            for (int64_t base = p0; base < p1; base += TILE) {
+            for (int64_t base = p0; base < p1; base += TILE, ++chunk) {
+                if ((chunk % NWARPS) != warp) continue;
                 const int64_t j = base + lane;
                 __syncwarp();
                 if (j < p1) {
@@ -229,7 +241,7 @@ template <int M, bool SELF>
 __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall c) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_tile;
-    __shared__ double s_cap[4];  // centre (x, y, z), query radius
+    __shared__ double s_cap[5];  // cap query: phi_c, dphi, first band, last band, full
     __shared__ float sE2[TPCF_MAX_BINS + 1];
     __shared__ unsigned char slut[CAT_LUT];
     const int K = g.K;
@@ -315,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS) cat_count_kernel(CatDev g, const flo
                                                              long long hi, int* counter,
                                                              unsigned long long* counts) {
     __shared__ int s_tile;
-    __shared__ double s_cap[4];
+    __shared__ double s_cap[5];
     __shared__ float sE2[TPCF_MAX_BINS + 1];
     __shared__ unsigned char slut[CAT_LUT];
     __shared__ __align__(16) float4 sCh[NWARPS * TILE];
