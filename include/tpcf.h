@@ -25,7 +25,8 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *    Calls enqueue work on it and return; they do not synchronise unless stated.
  *  - Calls never abort: they return a tpcf_status.  Errors found on the device are
- *    latched in the plan and reported by the next call or by tpcf_plan_sync().
+ *    latched in the plan's device status word and reported by tpcf_plan_sync()
+ *    (and by tpcf_run_host, which synchronises).
  *  - d_delta and d_w are float32, one value per point (RING pixel order for maps,
  *    catalogue order for catalogues).  w = 0 marks a masked point: it is neither a
  *    pivot nor a neighbour.

@@ -274,11 +274,6 @@ extern "C" int64_t tpcf_plan_npoints(tpcf_plan plan) { return plan ? plan->npoin
 
 extern "C" int64_t tpcf_plan_kernel_launches(tpcf_plan plan) { return plan ? plan->launches : -1; }
 
-static tpcf_status latched(tpcf_plan_s* P) {
-    (void)P;
-    return TPCF_OK;
-}
-
 static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
                                double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s) {
     const MapDev& g = P->map;
@@ -311,8 +306,6 @@ extern "C" tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const 
                                     void* stream) {
     if (!plan || !d_delta || !d_w || !d_zeta || !d_norm) return TPCF_ERR_INVALID_ARG;
     if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
-    tpcf_status st = latched(plan);
-    if (st != TPCF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     if (plan->kind == PLAN_MAP) return map_forward(plan, d_delta, d_w, pivot_begin, pivot_end, d_zeta, d_norm,
@@ -370,8 +363,6 @@ extern "C" tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const
                                      float* d_grad, void* stream) {
     if (!plan || !d_delta || !d_w || !d_norm || !d_dL_dzeta || !d_grad) return TPCF_ERR_INVALID_ARG;
     if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
-    tpcf_status st = latched(plan);
-    if (st != TPCF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     if (plan->kind == PLAN_MAP)

@@ -99,16 +99,7 @@ inline __host__ __device__ int n_entries(int K, int M) {
 
 // Device status bits.
 constexpr int ST_BAD_TILE = 1;
-constexpr int ST_ROW_OVERFLOW = 2;
+constexpr int ST_ROW_OVERFLOW = 2;   // informational: a row wider than the warp buffer used direct global adds
 constexpr int ST_TC_TIMEOUT_BIT = 4;  // a tensor-core completion wait gave up
-
-// Launchers generated per M in map_inst.cu (compiled once per TPCF_M value).
-typedef cudaError_t (*map_launch_fn)(const MapDev& g, const MapCall& c, int grid, cudaStream_t s);
-size_t map_fwd_smem(int K, int M);
-size_t map_bwd_smem(int K, int M);
-map_launch_fn map_fwd_launcher(int M);
-map_launch_fn map_bwd_launcher(int M);
-int map_fwd_blocks_per_sm(int M, size_t smem);
-int map_bwd_blocks_per_sm(int M, size_t smem);
 
 }  // namespace tpcf
