@@ -44,7 +44,7 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 MAP_WORKLOADS = ("fullsky_nside4096", "masked_map_nside1024", "fullsky_nside512", "map_nside64",
                  "fullsky_nside4096_paper")
-# The paper's exact-path timing (Sec. 4): ~40 min for one Nside 4096 map, 20 log bins over
+# The paper's exact-path timing (Sec. 3.2): ~40 min for one Nside 4096 map, 20 log bins over
 # 8-200 arcmin, m <= 8, forward only, one 128-thread CPU node; with the 3.42e13 in-bin
 # pairs of that shape (N^2 (cos 8' - cos 200') / 2) that is 1.43e10 pairs/s.
 PAPER_FWD_PAIRS_PER_S = {"fullsky_nside4096_paper": 3.42e13 / 2400.0}
@@ -126,16 +126,25 @@ def cat_flops_per_pair(M: int):
 
 # DRAM bytes per pixel per launch of the map kernels, from the ncu capture of the
 # Nside 512 case (profiles/map_kernels_fullsky_nside512.md: dram__bytes_read.sum +
-# dram__bytes_write.sum / pixels), valid only for the kernel source it was taken on.
-TRAFFIC = {"map_bwd_kernel": (18.24, "aef844b129b8dbdc"), "map_fwd_kernel": (19.26, "aef844b129b8dbdc")}
+# dram__bytes_write.sum / pixels), valid only for the kernel code it was taken on:
+# the key is a hash of map_kernels.cuh with comments and blank lines removed.
+TRAFFIC = {"map_bwd_kernel": (18.24, "d47ddc5e2ada9427"), "map_fwd_kernel": (19.26, "d47ddc5e2ada9427")}
+
+
+def kernel_code_hash(path):
+    import hashlib
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def traffic_per_launch(kernel, npix):
-    import hashlib
     bpp, sha = TRAFFIC[kernel]
     src = os.path.join(ROOT, "paper_2408_16847_gb300", "csrc", "map_kernels.cuh")
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return bpp * npix if cur == sha else None
+    return bpp * npix if kernel_code_hash(src) == sha else None
 
 
 def fp32_peak_tflops(clk):

@@ -4,24 +4,26 @@
 //
 // Work decomposition (forward):
 //   * a tile is 32 consecutive pivots of one HEALPix ring, one pivot per lane;
-//   * a CTA of 8 warps owns one tile at a time (persistent CTAs pull tiles from an
-//     atomic counter); for every radial bin k the warps split the neighbour rings
-//     that can hold bin-k pixels;
+//   * a CTA of 8 warps owns one tile at a time (persistent CTAs, 3 per SM, pull
+//     tiles from an atomic counter); for every radial bin k the warps split the
+//     neighbour rings that can hold bin-k pixels;
 //   * on a neighbour ring the bin-k pixels of a pivot form at most two contiguous
-//     runs, found from the per-ring-pair edge offsets T_e built by the plan
-//     (exact ring-range disc query, section 3.2 of the plan's design notes); each
-//     lane walks its own runs, so the bin is known without a per-pixel test and the
-//     (M+1) complex accumulators of the bin stay in registers across rings;
+//     runs, found from the per-ring-pair edge offsets T_e built by the plan (an
+//     exact ring-range disc query); each lane walks its own runs, so the bin is
+//     known without a per-pixel test and the (M+1) complex accumulators of the bin
+//     stay in registers across rings;
 //   * within a run e^{-i m phi} comes from the Chebyshev recurrences
 //     cos(m phi) = 2 cos(phi) cos((m-1) phi) - cos((m-2) phi) (same for sin), the
-//     trig-free harmonic step the paper uses (section 3.2, two operations per m),
-//     with the neighbour weight folded into the recurrence;
+//     trig-free harmonic step the paper describes (Sec. 3.1 and 3.2, two operations
+//     per m), with the neighbour weight folded into the recurrence and the cos and
+//     sin chains packed into one f32x2 FMA per step;
 //   * in the equatorial belt a neighbour ring has as many pixels as the pivot ring,
 //     so its pixels sit symmetrically about the pivot's meridian: the pixel at +phi
 //     and its mirror at -phi share one cos/sin evaluation and one recurrence;
 //   * after all bins, the tile's a_m^k(i) sit in shared memory and the CTA forms
 //     sum_i w_i d_i a^{k1} conj(a^{k2}) (eq. zetamEst2) and sum_i w_i W^{k1} W^{k2},
-//     adding them in FP64 into a slot owned by the CTA.
+//     adding them in FP64 into a slot owned by the CTA (FP32 pipe, or the tensor
+//     cores in map_fwd_tc_kernel).
 #pragma once
 
 #include <math.h>

@@ -216,7 +216,7 @@ def fullsky_nside4096() -> MapWorkload:
 
 
 def fullsky_nside4096_paper() -> MapWorkload:
-    """The shape of the paper's own timing (Sec. 4): Nside 4096, 20 log bins over
+    """The shape of the paper's own timing (Sec. 3.2): Nside 4096, 20 log bins over
     8-200 arcmin, m <= 8; the field is the full-sky bump recipe."""
     return MapWorkload("fullsky_nside4096_paper", 4096, log_bins(8.0 / 60.0, 200.0 / 60.0, 20, 8), 1_000_000,
                        (0.05, 1.0), seed=BASE_SEED + 5, cot_seed=BASE_SEED + 107)
