@@ -269,3 +269,29 @@ def test_map_is_catalogue_of_centres():
     hi = np.array([len(l) for l in tree.query_ball_point(xyz, ce[1] * (1 - 1e-12))])
     lo = np.array([len(l) for l in tree.query_ball_point(xyz, ce[0] * (1 - 1e-12))])
     np.testing.assert_array_equal(cnt, hi - lo)
+
+
+def test_r1_normalisation_of_a_constant_field(cap_case):
+    """R1 (eq. Xm.binned's prefactor: each pivot's moments over the weight of all its
+    neighbours, then eq. zetamEst's 1/sum w) for delta = c: zeta_0(k1,k2) =
+    c^3 sum_i w_i W^k1(i) W^k2(i) / Wtot(i)^2 / sum_i w_i, with the per-pivot bin weights
+    taken from cKDTree counts (independent of the oracle's neighbour search)."""
+    xyz, _, w, edges, M = cap_case
+    c = -0.8
+    r1 = oracle.zeta(xyz, np.full(len(xyz), c), w, edges, M, norm="R1")
+    ce = 2 * np.sin(np.deg2rad(edges) / 2)
+    tree = cKDTree(xyz)
+    K = len(edges) - 1
+    Wc = np.zeros((len(xyz), K))
+    for e in range(K + 1):
+        lists = tree.query_ball_point(xyz, ce[e] * (1 - 1e-12))
+        cumw = np.array([w[l].sum() - w[i] for i, l in enumerate(lists)])
+        if e > 0:
+            Wc[:, e - 1] += cumw
+        if e < K:
+            Wc[:, e] -= cumw
+    tot = Wc.sum(axis=1)
+    live = tot > 0
+    ref = c ** 3 * np.einsum("i,ik,il->kl", w[live], Wc[live] / tot[live, None], Wc[live] / tot[live, None]) / w.sum()
+    np.testing.assert_allclose(r1["zeta"][0].real, ref, rtol=1e-11, atol=1e-14)
+    assert np.abs(r1["zeta"][0].imag).max() < 1e-14
