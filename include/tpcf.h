@@ -165,7 +165,9 @@ tpcf_status tpcf_forward_noalloc(tpcf_plan plan, const float* d_delta, const flo
  * Adjoint: d_grad[p] = dL/d(delta_p) for a real loss L of zeta over the same pivot
  * range, given d_dL_dzeta = dL/dRe(zeta) + i dL/dIm(zeta) (zeta layout) and the
  * normalisation d_norm from the matching forward.  Recomputes the moments a_m^k
- * instead of storing them.  d_grad (float[npoints]) is overwritten.
+ * instead of storing them.  With TPCF_SELF_PAIRS_SUBTRACT the derivative of the
+ * subtracted diagonal is included.  d_grad (float[npoints]) is overwritten.  Map
+ * plans only (catalogue plans: TPCF_ERR_UNSUPPORTED).
  */
 tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const float* d_w,
                           int64_t pivot_begin, int64_t pivot_end, const double* d_norm,

@@ -195,7 +195,7 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     TRY_CUDA(P->alloc(&P->sums, P->nent));
     TRY_CUDA(P->alloc(&P->counter, 4));
     TRY_CUDA(P->alloc(&P->status, 4));
-    TRY_CUDA(P->alloc(&P->H, (size_t)(P->M + 1) * K * K * 2));
+    TRY_CUDA(P->alloc(&P->H, (size_t)(P->M + 1) * K * K * 2 + K));  // H, then cdiag (self-pair mode)
     TRY_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int) * 4, s));
     TRY_CUDA(cudaStreamSynchronize(s));
     return TPCF_OK;
@@ -336,13 +336,10 @@ extern "C" tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_
 static tpcf_status map_backward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
                                 const double* d_norm, const double* d_dL, float* d_grad, cudaStream_t s) {
     const MapDev& g = P->map;
-    if (P->flags & TPCF_SELF_PAIRS_SUBTRACT) {
-        snprintf(g_last_error, sizeof(g_last_error), "adjoint with self-pair subtraction");
-        return TPCF_ERR_UNSUPPORTED;
-    }
     pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_delta, d_w, P->wdw, g.npix);
     const int nout = (P->M + 1) * P->K * P->K;
-    adjoint_prep_kernel<<<n_blocks(nout, 128), 128, 0, s>>>(d_dL, d_norm, P->K, P->M, P->H);
+    const int self = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
+    adjoint_prep_kernel<<<n_blocks(nout, 128), 128, 0, s>>>(d_dL, d_norm, P->K, P->M, P->H, self);
     zero_f32_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_grad, g.npix);
     P->launches += 4;  // pack, prep, zero, adjoint
     TRY_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(int), s));
@@ -354,6 +351,7 @@ static tpcf_status map_backward(tpcf_plan_s* P, const float* d_delta, const floa
     c.status = P->status;
     c.H = P->H;
     c.grad = d_grad;
+    c.self_subtract = self;
     TRY_CUDA(kLaunch[P->M].bwd(g, c, P->bwd_grid, s));
     return TPCF_OK;
 }

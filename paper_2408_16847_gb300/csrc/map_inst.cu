@@ -31,10 +31,17 @@ cudaError_t TPCF_CAT(map_fwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c
 cudaError_t TPCF_CAT(map_bwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid,
                                                cudaStream_t s) {
     const size_t smem = bwd_tile_floats<TPCF_M>(g.K) * sizeof(float);
-    auto* k = map_bwd_kernel<TPCF_M>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, NTHREADS, smem, s>>>(g, c);
+    if (c.self_subtract) {
+        auto* k = map_bwd_kernel<TPCF_M, true>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    } else {
+        auto* k = map_bwd_kernel<TPCF_M, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, NTHREADS, smem, s>>>(g, c);
+    }
     return cudaGetLastError();
 }
 
@@ -56,8 +63,12 @@ int TPCF_CAT(map_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
 int TPCF_CAT(map_bwd_occupancy_m, TPCF_M)(int K) {
     const size_t smem = bwd_tile_floats<TPCF_M>(K) * sizeof(float);
     int nb = 0;
-    cudaFuncSetAttribute(map_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_bwd_kernel<TPCF_M>, NTHREADS, smem);
+    cudaFuncSetAttribute(map_bwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_bwd_kernel<TPCF_M, false>, NTHREADS, smem);
+    int nb_self = 0;
+    cudaFuncSetAttribute(map_bwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_self, map_bwd_kernel<TPCF_M, true>, NTHREADS, smem);
+    if (nb_self < nb) nb = nb_self;
     return nb;
 }
 

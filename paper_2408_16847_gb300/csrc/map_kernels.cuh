@@ -1097,10 +1097,10 @@ __device__ __forceinline__ void adj_harmonics2(const float2 (&h)[M + 1], float c
     Yb = xyb.y;
 }
 
-template <int M, bool FAST>
+template <int M, bool FAST, bool SELF = false>
 __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
-                                        int a, int len, const float2 (&h)[M + 1],
-                                        float wdi, const RowSink& s) {
+                                        int a, int len, const float2 (&h)[M + 1], float wdi, const RowSink& s,
+                                        float ck = 0.0f) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
@@ -1117,16 +1117,20 @@ __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restri
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
         adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
+        if (SELF) {  // self-pair subtraction: -2 cdiag_k (w_p d_p) per neighbour p
+            Xa = fmaf(ck, v0.x, Xa);
+            Xb = fmaf(ck, v1.x, Xb);
+        }
         if (on0) sink_add(s, a + t, idx, wdi * v0.y * (Xa + Ya));
         if (on1) sink_add(s, a + t + 1, idx1, wdi * v1.y * (Xb + Yb));
         idx = idx1 + 1 >= R.n ? idx1 + 1 - R.n : idx1 + 1;
     }
 }
 
-template <int M, bool FAST>
+template <int M, bool FAST, bool SELF = false>
 __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
                                           int a, int len, int mb, const float2 (&h)[M + 1], float wdi,
-                                          const RowSink& s) {
+                                          const RowSink& s, float ck = 0.0f) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
@@ -1148,12 +1152,12 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
         adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
         if (on0) {
-            sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya));
-            sink_add(s, mb - a - t, im_, wdi * m0.y * (Xa - Ya));
+            sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya + (SELF ? ck * p0.x : 0.0f)));
+            sink_add(s, mb - a - t, im_, wdi * m0.y * (Xa - Ya + (SELF ? ck * m0.x : 0.0f)));
         }
         if (on1) {
-            sink_add(s, a + t + 1, ip1, wdi * p1.y * (Xb + Yb));
-            sink_add(s, mb - a - t - 1, im1, wdi * m1.y * (Xb - Yb));
+            sink_add(s, a + t + 1, ip1, wdi * p1.y * (Xb + Yb + (SELF ? ck * p1.x : 0.0f)));
+            sink_add(s, mb - a - t - 1, im1, wdi * m1.y * (Xb - Yb + (SELF ? ck * m1.x : 0.0f)));
         }
         ip = ip1 + 1 >= R.n ? ip1 + 1 - R.n : ip1 + 1;
         im_ = im1 - 1 < 0 ? im1 - 1 + R.n : im1 - 1;
@@ -1161,10 +1165,11 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
 }
 
 // Neighbour legs of one ring r for the warp's lanes (all bins of r).
-template <int M>
+template <int M, bool SELF = false>
 __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, int r, int q, float wdi,
                                          const float2* __restrict__ wdw, const float* sH, float* rowbuf,
-                                         float* grad, int* status) {
+                                         float* grad, int* status,
+                                         const float* cdiag = nullptr) {
     const int lane = threadIdx.x & 31;
     const long long pr = P.pair0 + (r - P.rlo);
     const int2 TK = g.pair_T[pr * (g.K + 1) + g.K];
@@ -1216,6 +1221,7 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
         }
         const bool sym = (R.n == P.n_i) && (Tk1.x != T_INF);
         const BinRuns b = bin_runs(c, Tk, Tk1, g.E[k], g.E[k + 1], x, R.n, sym);
+        const float ck = SELF ? -2.0f * cdiag[k] : 0.0f;
         if (sym) {
             if (b.centre) {
                 const int p = c.cint;
@@ -1224,22 +1230,23 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
                 float cph, sph, X, Y;
                 pixel_dir<false>(0.0f, 0.0f, -c.cfrac * R.inv_n, R, cph, sph);
                 adj_harmonics<M>(h, cph, sph, X, Y);
+                if (SELF) X = fmaf(ck, v.x, X);
                 sink_add(s, p, pw, wdi * v.y * (X + Y));
             }
             const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
             if (fast)
-                adj_pairs<M, true>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s);
+                adj_pairs<M, true, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
             else
-                adj_pairs<M, false>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s);
+                adj_pairs<M, false, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
         } else {
             const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
             const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
             if (fast) {
-                adj_run<M, true>(R, wdw, c, b.a0, b.n0, h, wdi, s);
-                adj_run<M, true>(R, wdw, c, b.a1, b.n1, h, wdi, s);
+                adj_run<M, true, SELF>(R, wdw, c, b.a0, b.n0, h, wdi, s, ck);
+                adj_run<M, true, SELF>(R, wdw, c, b.a1, b.n1, h, wdi, s, ck);
             } else {
-                adj_run<M, false>(R, wdw, c, b.a0, b.n0, h, wdi, s);
-                adj_run<M, false>(R, wdw, c, b.a1, b.n1, h, wdi, s);
+                adj_run<M, false, SELF>(R, wdw, c, b.a0, b.n0, h, wdi, s, ck);
+                adj_run<M, false, SELF>(R, wdw, c, b.a1, b.n1, h, wdi, s, ck);
             }
         }
     }
@@ -1267,8 +1274,11 @@ __host__ __device__ inline size_t bwd_tile_floats(int K) {
     return p12 > p3 ? p12 : p3;
 }
 
-// One adjoint tile (all three phases).  Called by every thread of the CTA.
-template <int M>
+// One adjoint tile (all three phases).  Called by every thread of the CTA.  With
+// SELF (self-pair subtraction) the subtracted diagonal adds, per bin k with
+// cdiag_k = sum_m Re C_m(k,k), -w_p Q^k(p) cdiag_k to a pivot and
+// -2 w_p^2 d_p w_i d_i cdiag_k to each neighbour p of pivot i.
+template <int M, bool SELF = false>
 __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int tile, float* smem) {
     const int K = g.K;
     float* sA = smem;
@@ -1303,7 +1313,7 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
     }
     __syncthreads();
     // phase 1: the tile's moments, exactly as in the forward
-    tile_moments<M, false>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
+    tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
     __syncthreads();
     // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
     for (int m = 0; m <= M; ++m) {
@@ -1338,19 +1348,25 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
         }
         __syncthreads();
     }
+    const float* cdiag = SELF ? c.H + (size_t)(M + 1) * K * K * 2 : nullptr;
     if (threadIdx.x < TILE && in) {
-        const float gp = 0.5f * pv.y * sPrim[lane];
+        float gp = 0.5f * pv.y * sPrim[lane];
+        if (SELF) {
+            float t = 0.0f;
+            for (int k = 0; k < K; ++k) t = fmaf(cdiag[k], sQ[k * TILE + lane], t);
+            gp = fmaf(-pv.y, t, gp);
+        }
         if (gp != 0.0f) atomicAdd(c.grad + pix, gp);
     }
     __syncthreads();  // the row buffers of phase 3 overlay sPrim and the rest
     // phase 3: neighbour legs, warps split the neighbour rings
     const int2 rr = g.ring_range[P.i];
     for (int r = rr.x + warp; r <= rr.y; r += NWARPS)
-        adj_ring<M>(g, P, r, qg, pv.x, c.wdw, sA, sRow + (size_t)warp * ROW, c.grad, c.status);
+        adj_ring<M, SELF>(g, P, r, qg, pv.x, c.wdw, sA, sRow + (size_t)warp * ROW, c.grad, c.status, cdiag);
     __syncthreads();
 }
 
-template <int M>
+template <int M, bool SELF>
 __global__ void __launch_bounds__(NTHREADS, 3) map_bwd_kernel(MapDev g, MapCall c) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
@@ -1359,7 +1375,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) map_bwd_kernel(MapDev g, MapCall 
         __syncthreads();
         const int tile = s_tile;
         if ((long long)tile >= g.ntiles) break;
-        bwd_tile<M>(g, c, tile, smem);
+        bwd_tile<M, SELF>(g, c, tile, smem);
     }
 }
 

@@ -93,11 +93,20 @@ __device__ __forceinline__ void adjoint_prep_one(const double* __restrict__ dL, 
     H[2 * idx + 1] = (float)(-c1i + c2i);
 }
 
+// With self-pair subtraction H is followed by cdiag_k = sum_m Re dL_m(k,k) / D(k,k)
+// (the subtracted diagonal enters every m with the same real weight).
 __global__ void adjoint_prep_kernel(const double* __restrict__ dL, const double* __restrict__ norm, int K,
-                                    int M, float* H) {
+                                    int M, float* H, int with_diag) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (M + 1) * K * K) return;
     adjoint_prep_one(dL, norm, K, H, idx);
+    if (with_diag && idx < K) {
+        const double d = norm[idx * K + idx];
+        double t = 0.0;
+        if (d != 0.0)
+            for (int m = 0; m <= M; ++m) t += dL[2 * ((size_t)m * K * K + (size_t)idx * K + idx)] / d;
+        H[(size_t)(M + 1) * K * K * 2 + idx] = (float)t;
+    }
 }
 
 // ------------------------------------------------------------------ batches
