@@ -260,7 +260,18 @@ def setup_map(args, dev, rank):
 
     wl = map_workload(args.workload)
     t0 = time.time()
-    d32, w32 = map_inputs(wl, rank)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        # rank 0 paints the map once (cached in /dev/shm); the other ranks read the
+        # cache and add their own noise draw instead of painting concurrently
+        import torch.distributed as dist
+        if rank == 0:
+            d32, w32 = map_inputs(wl, rank)
+        dist.barrier()
+        if rank != 0:
+            d32, w32 = map_inputs(wl, rank)
+    else:
+        d32, w32 = map_inputs(wl, rank)
     log("[rank %d] inputs ready in %.1fs" % (rank, time.time() - t0))
     K, M = wl.bins.nbins, wl.bins.m_max
     plan = tpcf.Plan.map(wl.nside, wl.bins.edges_deg, M, contract=args.contract)
