@@ -466,6 +466,27 @@ def setup_batch(args, dev, rank):
         if ev is not None:
             ev.record(torch.cuda.current_stream())
 
+    # e2e: every map's delta, w and dL/dzeta from pinned host memory into the batch's
+    # device buffers, one graph replay, zeta, norm and the gradients back to the host
+    h_in = [(x.cpu().pin_memory(), y.cpu().pin_memory(), z.cpu().pin_memory()) for x, y, z in zip(ds, ws, dls)]
+    h_out = [(torch.empty_like(z, device="cpu").pin_memory(), torch.empty_like(n, device="cpu").pin_memory(),
+              torch.empty_like(g, device="cpu").pin_memory()) for z, n, g in zip(zs, ns, gs)]
+
+    def e2e_step():
+        for (hd, hw, hl), d, w, l in zip(h_in, ds, ws, dls):
+            d.copy_(hd, non_blocking=True)
+            w.copy_(hw, non_blocking=True)
+            l.copy_(hl, non_blocking=True)
+        batch.launch()
+        for (oz, on, og), z, n, g in zip(h_out, zs, ns, gs):
+            oz.copy_(z, non_blocking=True)
+            on.copy_(n, non_blocking=True)
+            og.copy_(g, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_in = sum(a.numel() * a.element_size() for t in h_in for a in t)
+    e2e_out = sum(a.numel() * a.element_size() for t in h_out for a in t)
+
     config = {"workload": "batched_maps", "maps": len(wls), "nsides": list(nsides),
               "bins": "8-24 lin/log bins over 0.2-4 deg", "m_max": "6-12",
               "pass": "forward + adjoint, one graph replay", "pairs_per_step_per_gpu": total,
@@ -474,7 +495,7 @@ def setup_batch(args, dev, rank):
               else "L2-resident inputs", "parallelism": "independent batch per GPU"}
     if nsides != (256, 512, 1024, 2048):
         config["scaled"] = "Nside set scaled down from 256/512/1024/2048"
-    return dict(step=step, split=("batch", None), pairs=total, e2e=None, e2e_bytes=(0, 0),
+    return dict(step=step, split=("batch", None), pairs=total, e2e=e2e_step, e2e_bytes=(e2e_in, e2e_out),
                 launches=plans[0].kernel_launches, config=config, cpu_baseline=None,
                 roofline=lambda t1, t2, clk: {"bound": "alu", "kernel": "batch_bwd_kernel",
                                               "achieved": flops / (t1 * 1e-3) / 1e12,

@@ -103,8 +103,7 @@ tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const tpcf_bins*
  * (fp32 chord from hi/lo coordinates, FP64 decision within 2e-6 of an edge).  The
  * plan keeps its own sorted copy: d_xyz may be freed once the call has returned.
  * Forward calls take d_delta / d_w in the caller's point order, and pivot ranges are
- * ranges of caller indices.  The adjoint is map-only (TPCF_ERR_UNSUPPORTED).
- * 1 <= n <= 2^31 - 1, else TPCF_ERR_INVALID_ARG.
+ * ranges of caller indices.  1 <= n <= 2^31 - 1, else TPCF_ERR_INVALID_ARG.
  */
 tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_xyz, int64_t n,
                                      const tpcf_bins* bins, void* stream);
@@ -166,8 +165,9 @@ tpcf_status tpcf_forward_noalloc(tpcf_plan plan, const float* d_delta, const flo
  * range, given d_dL_dzeta = dL/dRe(zeta) + i dL/dIm(zeta) (zeta layout) and the
  * normalisation d_norm from the matching forward.  Recomputes the moments a_m^k
  * instead of storing them.  With TPCF_SELF_PAIRS_SUBTRACT the derivative of the
- * subtracted diagonal is included.  d_grad (float[npoints]) is overwritten.  Map
- * plans only (catalogue plans: TPCF_ERR_UNSUPPORTED).
+ * subtracted diagonal is included (map plans; catalogue plans with self-pair
+ * subtraction return TPCF_ERR_UNSUPPORTED).  d_grad (float[npoints], caller order for
+ * catalogues) is overwritten.
  */
 tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const float* d_w,
                           int64_t pivot_begin, int64_t pivot_end, const double* d_norm,

@@ -35,6 +35,8 @@ cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, l
 tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaStream_t s);
 tpcf_status catalog_count(tpcf_plan_s* P, const float* d_w, int64_t lo, int64_t hi, int64_t* d_counts,
                           cudaStream_t s);
+tpcf_status catalog_backward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
+                             const double* d_norm, const double* d_dL, float* d_grad, cudaStream_t s);
 tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
                             double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s);
 
@@ -365,6 +367,8 @@ extern "C" tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const
     plan->last_stream = s;
     if (plan->kind == PLAN_MAP)
         return map_backward(plan, d_delta, d_w, pivot_begin, pivot_end, d_norm, d_dL_dzeta, d_grad, s);
+    if (plan->kind == PLAN_CATALOG)
+        return catalog_backward(plan, d_delta, d_w, pivot_begin, pivot_end, d_norm, d_dL_dzeta, d_grad, s);
     return TPCF_ERR_UNSUPPORTED;
 }
 

@@ -164,9 +164,10 @@ __device__ __forceinline__ void cat_tile_cap(const CatDev& g, bool live, double 
     }
 }
 
-// Every candidate of the cap for this warp (bands round-robin over the warps), with
-// its bin k (-1 below the first edge, K beyond the last), the chord vector from the
-// lane's pivot and its (w d, w): f(k, dx, dy, dz, v).  Candidates are staged 32 at a
+// Every candidate of the cap for this warp, with its bin k (-1 below the first edge,
+// K beyond the last), the chord vector from the lane's pivot, its (w d, w) and its
+// sorted index: f(k, dx, dy, dz, v, j).  Calls are warp-uniform (every lane sees the
+// same candidate at the same time).  Candidates are staged 32 at a
 // time in the warp's shared buffers wh / wl / wv.
 template <class F>
 __device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restrict__ wdw, const double* s_cap,
@@ -230,7 +231,7 @@ __device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restri
                     const int e1 = max(k, 0), e2 = min(k + 1, K);
                     if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
                         k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.px, P.py, P.pz);
-                    f(k, dx, dy, dz, wv[u]);
+                    f(k, dx, dy, dz, wv[u], __float_as_int(ql.w));
                 }
             }
         }
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
         float W = 0.0f, Qs = 0.0f, QW = 0.0f;
         int kcur = -1;
         cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
-                 [&](int k, float dx, float dy, float dz, float2 v) {
+                 [&](int k, float dx, float dy, float dz, float2 v, int) {
                      const bool on = k >= 0 && k < K;
                      if (on && k != kcur) {
                          if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
@@ -316,6 +317,167 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
         if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
         __syncthreads();
         tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+        __syncthreads();
+    }
+}
+
+// Shared memory of the catalogue adjoint: the forward's, plus one m of H and the
+// primary-term sums.
+template <int M>
+__host__ __device__ inline size_t cat_bwd_bytes(int K) {
+    return cat_tile_bytes<M>(K) + ((size_t)K * K * 2 + TILE) * sizeof(float);
+}
+
+// Catalogue adjoint, dL/d(delta_p) (the map adjoint's three phases on the catalogue
+// walk): phase 1 recomputes the tile's moments, phase 2 forms h = H conj(a) in place
+// and the primary term, phase 3 walks the candidates again and adds
+// w_j w_i d_i sum_m (cos(m phi) Re h_m^k + sin(m phi) Im h_m^k) for every in-bin pair;
+// the 32 pivots' contributions to one candidate are summed across the warp before one
+// atomic add to its gradient.
+template <int M>
+__global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall c) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_tile;
+    __shared__ double s_cap[5];
+    __shared__ float sE2[TPCF_MAX_BINS + 1];
+    __shared__ unsigned char slut[CAT_LUT];
+    const int K = g.K;
+    float* sA = smem;
+    float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
+    float* sQ = sW + K * TILE;
+    float* sQW = sQ + K * TILE;
+    float* sPiv = sQW + K * TILE;
+    float4* sCh = reinterpret_cast<float4*>(smem + tile_floats<M>(K));
+    float4* sCl = sCh + NWARPS * TILE;
+    float2* sCv = reinterpret_cast<float2*>(sCl + NWARPS * TILE);
+    float* sHm = reinterpret_cast<float*>(sCv + NWARPS * TILE);  // [K][K][2], one m at a time
+    float* sPrim = sHm + (size_t)K * K * 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t nfl = tile_floats<M>(K) - 2 * TILE;
+    for (int e = threadIdx.x; e <= K; e += NTHREADS) sE2[e] = g.E2[e];
+    for (int e = threadIdx.x; e < CAT_LUT; e += NTHREADS) slut[e] = g.lut[e];
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if ((long long)tile >= g.ntiles) break;
+        const int64_t si = (int64_t)tile * TILE + lane;
+        bool live = false;
+        float2 pv = make_float2(0.0f, 0.0f);
+        double px = 0.0, py = 0.0, pz = 1.0;
+        int64_t oi = -1;
+        if (si < g.n) {
+            oi = g.orig[si];
+            if (oi >= c.piv_lo && oi < c.piv_hi) {
+                pv = c.wdw[si];
+                live = pv.y != 0.0f;
+                if (!live) pv = make_float2(0.0f, 0.0f);
+            }
+            px = g.xyz[3 * si];
+            py = g.xyz[3 * si + 1];
+            pz = g.xyz[3 * si + 2];
+        }
+        if (!__syncthreads_or(live)) continue;
+        for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
+        if (threadIdx.x < TILE) {
+            sPiv[lane] = pv.x;
+            sPiv[TILE + lane] = pv.y;
+            sPrim[lane] = 0.0f;
+        }
+        if (warp == 0) cat_tile_cap(g, live, px, py, pz, s_cap);
+        __syncthreads();
+        const CatPivot P = cat_pivot(px, py, pz);
+
+        // phase 1: the moments, as in the forward
+        {
+            float2 acc[M + 1];
+#pragma unroll
+            for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
+            float W = 0.0f, Qs = 0.0f, QW = 0.0f;
+            int kcur = -1;
+            cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+                     [&](int k, float dx, float dy, float dz, float2 v, int) {
+                         const bool on = k >= 0 && k < K;
+                         if (on && k != kcur) {
+                             if (kcur >= 0) cat_flush<M, false>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
+                             kcur = k;
+                         }
+                         const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                         const float E = fmaf(dx, P.ex, dy * P.ey);
+                         const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                         const float wd = on ? v.x : 0.0f;
+                         harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
+                         W += on ? v.y : 0.0f;
+                     });
+            if (kcur >= 0) cat_flush<M, false>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
+        }
+        __syncthreads();
+        // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
+        for (int m = 0; m <= M; ++m) {
+            for (int e = threadIdx.x; e < K * K * 2; e += NTHREADS) sHm[e] = c.H[(size_t)m * K * K * 2 + e];
+            __syncthreads();
+            float hrv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
+            float hiv[(TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS];
+            int nmine = 0;
+            for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
+                const int k = e / TILE, l = e - k * TILE;
+                float hr = 0.0f, hi = 0.0f;
+                for (int kp = 0; kp < K; ++kp) {
+                    const float Hr = sHm[(k * K + kp) * 2], Hi = sHm[(k * K + kp) * 2 + 1];
+                    const float* ap = sA + ((size_t)kp * (M + 1) + m) * 2 * TILE;
+                    const float tr = ap[l], ti = ap[TILE + l];
+                    hr = fmaf(Hr, tr, fmaf(-Hi, ti, hr));
+                    hi = fmaf(Hr, ti, fmaf(Hi, tr, hi));
+                }
+                const float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+                atomicAdd(sPrim + l, fmaf(ak[l], hr, ak[TILE + l] * hi));
+                hrv[nmine] = hr;
+                hiv[nmine] = hi;
+            }
+            __syncthreads();
+            nmine = 0;
+            for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
+                const int k = e / TILE, l = e - k * TILE;
+                float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+                ak[l] = hrv[nmine];
+                ak[TILE + l] = hiv[nmine];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < TILE && live) {
+            const float gp = 0.5f * pv.y * sPrim[lane];
+            if (gp != 0.0f) atomicAdd(c.grad + oi, gp);
+        }
+        // phase 3: the neighbour legs, summed over the warp's 32 pivots per candidate
+        {
+            float2 h[M + 1];
+            int kh = -1;
+            const float wdi = pv.x;
+            cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+                     [&](int k, float dx, float dy, float dz, float2 v, int j) {
+                         const bool on = k >= 0 && k < K && wdi != 0.0f;
+                         float val = 0.0f;
+                         if (on) {
+                             if (k != kh) {
+                                 const float* hk = sA + (size_t)k * (M + 1) * 2 * TILE;
+#pragma unroll
+                                 for (int m = 0; m <= M; ++m)
+                                     h[m] = make_float2(hk[(2 * m) * TILE + lane], hk[(2 * m + 1) * TILE + lane]);
+                                 kh = k;
+                             }
+                             const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                             const float E = fmaf(dx, P.ex, dy * P.ey);
+                             const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                             float X, Y;
+                             adj_harmonics<M>(h, N * rinv, E * rinv, X, Y);
+                             val = wdi * v.y * (X + Y);
+                         }
+#pragma unroll
+                         for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                         if (lane == 0 && val != 0.0f) atomicAdd(c.grad + g.orig[j], val);
+                     });
+        }
         __syncthreads();
     }
 }
@@ -358,7 +520,7 @@ __global__ void __launch_bounds__(NTHREADS) cat_count_kernel(CatDev g, const flo
         const CatPivot P = cat_pivot(px, py, pz);
         unsigned long long cnt = 0;
         cat_walk(g, wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
-                 [&](int k, float, float, float, float2) { cnt += (k >= 0 && k < K) ? 1ull : 0ull; });
+                 [&](int k, float, float, float, float2, int) { cnt += (k >= 0 && k < K) ? 1ull : 0ull; });
         cnt = live ? cnt : 0ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);

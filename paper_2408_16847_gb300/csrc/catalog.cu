@@ -22,7 +22,9 @@ namespace tpcf {
 // per-M catalogue launchers (map_inst.cu)
 #define TPCF_DECL_CAT_M(m)                                                                     \
     cudaError_t cat_fwd_launch_m##m(const CatDev&, const MapCall&, int, cudaStream_t);        \
-    int cat_fwd_occupancy_m##m(int, int);
+    int cat_fwd_occupancy_m##m(int, int);                                                     \
+    cudaError_t cat_bwd_launch_m##m(const CatDev&, const MapCall&, int, cudaStream_t);        \
+    int cat_bwd_occupancy_m##m(int);
 TPCF_DECL_CAT_M(0) TPCF_DECL_CAT_M(1) TPCF_DECL_CAT_M(2) TPCF_DECL_CAT_M(3) TPCF_DECL_CAT_M(4)
 TPCF_DECL_CAT_M(5) TPCF_DECL_CAT_M(6) TPCF_DECL_CAT_M(7) TPCF_DECL_CAT_M(8) TPCF_DECL_CAT_M(9)
 TPCF_DECL_CAT_M(10) TPCF_DECL_CAT_M(11) TPCF_DECL_CAT_M(12) TPCF_DECL_CAT_M(13) TPCF_DECL_CAT_M(14)
@@ -32,8 +34,10 @@ TPCF_DECL_CAT_M(15) TPCF_DECL_CAT_M(16)
 struct CLaunch {
     cudaError_t (*fwd)(const CatDev&, const MapCall&, int, cudaStream_t);
     int (*occ)(int, int);
+    cudaError_t (*bwd)(const CatDev&, const MapCall&, int, cudaStream_t);
+    int (*bwd_occ)(int);
 };
-#define TPCF_CROW(m) {cat_fwd_launch_m##m, cat_fwd_occupancy_m##m}
+#define TPCF_CROW(m) {cat_fwd_launch_m##m, cat_fwd_occupancy_m##m, cat_bwd_launch_m##m, cat_bwd_occupancy_m##m}
 static const CLaunch kCat[TPCF_MAX_M + 1] = {
     TPCF_CROW(0),  TPCF_CROW(1),  TPCF_CROW(2),  TPCF_CROW(3),  TPCF_CROW(4),  TPCF_CROW(5),
     TPCF_CROW(6),  TPCF_CROW(7),  TPCF_CROW(8),  TPCF_CROW(9),  TPCF_CROW(10), TPCF_CROW(11),
@@ -226,6 +230,10 @@ tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaSt
         return TPCF_ERR_UNSUPPORTED;
     }
     P->fwd_grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)P->num_sms * occ));
+    const int occ_b = kCat[P->M].bwd_occ(K);
+    TRY_CUDA(cudaGetLastError());
+    P->bwd_grid = occ_b < 1 ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)P->num_sms * occ_b));
+    TRY_CUDA(P->alloc(&P->H, (size_t)(P->M + 1) * K * K * 2 + K));
     P->nent = n_entries(K, P->M);
     TRY_CUDA(P->alloc(&P->wdw, n));
     TRY_CUDA(P->alloc(&P->slots, (size_t)P->fwd_grid * P->nent));
@@ -251,6 +259,35 @@ tpcf_status catalog_count(tpcf_plan_s* P, const float* d_w, int64_t lo, int64_t 
     TRY_CUDA(cat_count_launch(g, P->wdw, lo, hi, P->counter, (unsigned long long*)d_counts, P->num_sms * 4, s));
     // every catalogue pair is visited singly: counts[2] = counts[0]
     TRY_CUDA(cudaMemcpyAsync(d_counts + 2, d_counts, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    return TPCF_OK;
+}
+
+tpcf_status catalog_backward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
+                             const double* d_norm, const double* d_dL, float* d_grad, cudaStream_t s) {
+    const CatDev& g = P->cat;
+    if (P->flags & TPCF_SELF_PAIRS_SUBTRACT) {
+        set_error("catalogue adjoint with self-pair subtraction");
+        return TPCF_ERR_UNSUPPORTED;
+    }
+    if (P->bwd_grid < 1) {
+        set_error("catalogue adjoint kernel does not fit on an SM");
+        return TPCF_ERR_UNSUPPORTED;
+    }
+    cat_pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(g.n, g.orig, d_delta, d_w, P->wdw);
+    const int nout = (P->M + 1) * P->K * P->K;
+    adjoint_prep_kernel<<<(nout + 127) / 128, 128, 0, s>>>(d_dL, d_norm, P->K, P->M, P->H, 0);
+    zero_f32_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_grad, g.n);
+    P->launches += 4;  // pack, prep, zero, adjoint
+    TRY_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(int), s));
+    MapCall c{};
+    c.wdw = P->wdw;
+    c.piv_lo = lo;
+    c.piv_hi = hi;
+    c.counter = P->counter;
+    c.status = P->status;
+    c.H = P->H;
+    c.grad = d_grad;
+    TRY_CUDA(kCat[P->M].bwd(g, c, P->bwd_grid, s));
     return TPCF_OK;
 }
 

@@ -203,6 +203,24 @@ int TPCF_CAT(cat_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
     return nb;
 }
 
+// Catalogue adjoint.
+cudaError_t TPCF_CAT(cat_bwd_launch_m, TPCF_M)(const CatDev& g, const MapCall& c, int grid, cudaStream_t s) {
+    const size_t smem = cat_bwd_bytes<TPCF_M>(g.K);
+    auto* k = cat_bwd_kernel<TPCF_M>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(g, c);
+    return cudaGetLastError();
+}
+
+int TPCF_CAT(cat_bwd_occupancy_m, TPCF_M)(int K) {
+    const size_t smem = cat_bwd_bytes<TPCF_M>(K);
+    int nb = 0;
+    cudaFuncSetAttribute(cat_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cat_bwd_kernel<TPCF_M>, NTHREADS, smem);
+    return nb;
+}
+
 #if TPCF_M == 0
 cudaError_t cat_count_launch(const CatDev& g, const float2* wdw, long long lo, long long hi, int* counter,
                              unsigned long long* counts, int grid, cudaStream_t s) {

@@ -166,3 +166,36 @@ def test_catalogue_pair_count_exact():
     assert sym == 0 and single == total
     t2, _, _ = plan.count_pairs(to_dev(np.ones_like(w)), (1000, 4000))
     assert t2 == int(oracle.pair_counts(xyz, edges, pivots=np.arange(1000, 4000)).sum())
+
+
+@pytest.mark.parametrize("n,edges,M,pivots", [
+    (3000, [3.1, 8.3, 15.7, 25.9], 6, None),
+    (6000, list(np.geomspace(1.1, 12.3, 6)), 10, (500, 2300)),
+])
+def test_catalogue_gradient_vs_oracle_and_fd(n, edges, M, pivots):
+    tpcf = _tpcf()
+    xyz = synth.clustered_catalog(n, 80, 2.0, synth.BASE_SEED + 980 + n)
+    d, w = _field(n, 981 + n)
+    K = len(edges) - 1
+    g = synth.rng(982)
+    cot = g.standard_normal((M + 1, K, K)) + 1j * g.standard_normal((M + 1, K, K))
+    plan = tpcf.Plan.catalog(_xyz_dev(xyz), np.asarray(edges), M)
+    dt, wt = to_dev(d), to_dev(w)
+    zeta, norm = plan.forward(dt, wt, pivots)
+    gl = torch.from_numpy(np.stack([cot.real, cot.imag], axis=-1)).to("cuda:0")
+    grad = plan.backward(dt, wt, norm, gl, pivots).cpu().numpy()
+    plan.sync()
+    piv = None if pivots is None else np.arange(pivots[0], pivots[1])
+    gref = oracle.gradient(xyz, d.astype(np.float64), w.astype(np.float64), np.asarray(edges), M, cot, pivots=piv)
+    scale = np.abs(gref).max()
+    assert scale > 0
+    assert np.abs(grad - gref).max() < TOL * scale
+
+    def L(dd):
+        z, _ = plan.forward(to_dev(dd), wt, pivots)
+        zc = tpcf.as_complex(z).cpu().numpy()
+        return float(np.sum(cot.real * zc.real + cot.imag * zc.imag))
+    for p in [1, n // 2, n - 3]:
+        dp = d.copy(); dp[p] += 1.0
+        dm = d.copy(); dm[p] -= 1.0
+        assert abs((L(dp) - L(dm)) / 2.0 - grad[p]) <= 1e-3 * scale, p
