@@ -14,7 +14,10 @@ Each test checks the oracle against something it does not compute itself:
   Hermitian symmetry, Im zeta_m(theta, theta) = 0 on the diagonal (section 3.4);
 * the adjoint: exact central differences (the loss is quadratic in each single
   d_p because a point is never its own neighbour) and Euler's identity for the
-  homogeneous cubic, sum_p d_p dL/dd_p = 3 L.
+  homogeneous cubic, sum_p d_p dL/dd_p = 3 L;
+* the catalogue D-R composition: data placed on the randoms' positions with a
+  constant weight cancel the randoms exactly (S = 0), and the d = 1 data-only
+  normalisation equals alpha^3 D_R.
 """
 import math
 
@@ -50,7 +53,8 @@ def _latlon(xyz):
 
 def brute_force_S(xyz, delta, w, edges_deg, M, keep_self=True):
     """Triplet sum  S_m(k1,k2) = sum_i w_i d_i sum_{j,l} w_j d_j w_l d_l
-    Theta_k1(ij) Theta_k2(il) exp(-i m (beta_ij - beta_il)),  beta = initial bearing."""
+    Theta_k1(ij) Theta_k2(il) exp(-i m (beta_ij - beta_il)),  beta = initial bearing.
+    The phase matrix of each pivot is raised to the m-th power elementwise."""
     lat, lon = _latlon(xyz)
     th_e = np.deg2rad(np.asarray(edges_deg))
     K = len(th_e) - 1
@@ -73,12 +77,26 @@ def brute_force_S(xyz, delta, w, edges_deg, M, keep_self=True):
         x = wd[sel]
         onehot = np.zeros((len(kk), K))
         onehot[np.arange(len(kk)), kk] = 1.0
+        E1 = np.exp(-1j * (beta[:, None] - beta[None, :]))
+        T = (x[:, None] * x[None, :]).astype(complex)
+        if not keep_self:
+            np.fill_diagonal(T, 0.0)
         for m in range(M + 1):
-            T = np.exp(-1j * m * (beta[:, None] - beta[None, :])) * (x[:, None] * x[None, :])
-            if not keep_self:
-                np.fill_diagonal(T, 0.0)
+            if m:
+                T = T * E1
             S[m] += wd[i] * (onehot.T @ T @ onehot)
     return S
+
+
+@pytest.fixture(scope="module")
+def brute_case():
+    """About 2000 points in a 10 deg cap, ~170 neighbours per pivot in 4 bins."""
+    xyz = _cap_points(2000, 10.0, seed=11)
+    g = synth.rng(12)
+    delta = g.standard_normal(len(xyz))
+    w = g.uniform(0.5, 1.5, len(xyz))
+    edges = np.array([0.6, 1.1, 1.7, 2.4, 3.2])
+    return xyz, delta, w, edges, 5
 
 
 @pytest.fixture(scope="module")
@@ -92,8 +110,8 @@ def cap_case():
 
 
 @pytest.mark.parametrize("keep", [True, False])
-def test_brute_force_triplets(cap_case, keep):
-    xyz, delta, w, edges, M = cap_case
+def test_brute_force_triplets(brute_case, keep):
+    xyz, delta, w, edges, M = brute_case
     res = oracle.zeta(xyz, delta, w, edges, M, self_pairs="keep" if keep else "subtract")
     assert res["min_margin"] > 1e-9  # no pair sits on a bin edge: both bin the same way
     Sb = brute_force_S(xyz, delta, w, edges, M, keep_self=keep)
@@ -295,3 +313,46 @@ def test_r1_normalisation_of_a_constant_field(cap_case):
     ref = c ** 3 * np.einsum("i,ik,il->kl", w[live], Wc[live] / tot[live, None], Wc[live] / tot[live, None]) / w.sum()
     np.testing.assert_allclose(r1["zeta"][0].real, ref, rtol=1e-11, atol=1e-14)
     assert np.abs(r1["zeta"][0].imag).max() < 1e-14
+
+
+def test_catalog_zeta_randoms_cancel_data():
+    """D-R composition, data at the randoms' positions with a constant weight c: then
+    alpha = sum w_D / n_R = c, and every position carries w d = c (data) and -alpha
+    (random), so every union moment a_m^k vanishes and S = 0 up to rounding.  A wrong
+    alpha or a sign slip on the randoms leaves S of the order of the data-only S."""
+    xyz = _cap_points(2000, 10.0, seed=31)
+    edges = np.array([0.6, 1.1, 1.7, 2.4, 3.2])
+    M = 4
+    for c in (1.0, 1.3):
+        wd = np.full(len(xyz), c)
+        res = oracle.catalog_zeta(xyz, wd, xyz, edges, M)
+        assert res["alpha"] == pytest.approx(c, rel=1e-15)
+        data_only = oracle.zeta(xyz, np.ones(len(xyz)), wd, edges, M)["S"]
+        scale = np.abs(data_only).max()
+        assert scale > 0
+        assert np.abs(res["S"]).max() < 1e-12 * scale
+
+
+def test_catalog_zeta_normalisation_is_alpha_cubed():
+    """Same layout (data at the randoms' positions, weight c): the D-R denominator
+    alpha^3 D_R must equal the d = 1 estimator run on the data alone, whose every
+    weight is c, i.e. sum_i c (c W^k1)(c W^k2) = c^3 D_R.  alpha or alpha^2 in place of
+    alpha^3 fails.  zeta is S over that denominator."""
+    xyz = _cap_points(2000, 10.0, seed=32)
+    edges = np.array([0.6, 1.1, 1.7, 2.4, 3.2])
+    M = 3
+    c = 1.7
+    wd = np.full(len(xyz), c)
+    res = oracle.catalog_zeta(xyz, wd, xyz, edges, M)
+    Dd = oracle.zeta(xyz, np.ones(len(xyz)), wd, edges, M)["D"]
+    np.testing.assert_allclose(res["D"], Dd, rtol=1e-12)
+    DR = oracle.zeta(xyz, np.ones(len(xyz)), np.ones(len(xyz)), edges, M)["D"]
+    assert np.abs(Dd - c ** 2 * DR).max() > 0.1 * np.abs(Dd).max()  # alpha^2 would be caught
+    # ratio: data at other positions; zeta = S / (alpha^3 D_R) entry by entry
+    xd = _cap_points(1500, 10.0, seed=33)
+    wd2 = synth.rng(34).uniform(0.5, 1.5, len(xd))
+    r2 = oracle.catalog_zeta(xd, wd2, xyz, edges, M)
+    alpha = wd2.sum() / len(xyz)
+    np.testing.assert_allclose(r2["D"], alpha ** 3 * DR, rtol=1e-12)
+    live = DR > 0
+    np.testing.assert_allclose(r2["zeta"][:, live], r2["S"][:, live] / (alpha ** 3 * DR[live])[None], rtol=1e-12)
