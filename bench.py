@@ -1,15 +1,17 @@
 #!/usr/bin/env python
 """Throughput of the harmonic 3PCF estimator on GB300: neighbour pairs/s.
 
-One step = one pass of the whole estimator over one batch of synthetic input:
+One step = one pass of the estimator over one batch of synthetic input:
 
   fullsky_nside4096 (default)  forward (neighbour search, binning, harmonics,
-                               contraction, normalisation) + adjoint dL/d(delta) of
-                               L = sum c Re zeta, HEALPix Nside 4096 (201,326,592
-                               pixels), 20 log bins 0.1-2 deg, m <= 10
-  masked_map_nside1024,
-  fullsky_nside512, map_nside64  the same pass on smaller maps (fullsky_nside512 is
-                               the case profiled with ncu)
+                               contraction, normalisation) over the whole HEALPix
+                               Nside 4096 map (201,326,592 pixels), 20 log bins
+                               0.1-2 deg, m <= 10.  The forward + adjoint dL/d(delta)
+                               of L = sum c Re zeta is timed beside it over
+                               --fb-steps full steps and reported under "parts".
+  masked_map_nside1024         forward + adjoint of the masked Nside 1024 map
+  fullsky_nside512, map_nside64  forward (+ adjoint part) on smaller maps
+                               (fullsky_nside512 is the case profiled with ncu)
   catalog_2e7                  catalogue D-R estimate: forward over 2e7 clustered
                                points + 6e7 randoms, forward over the randoms,
                                normalisation (16 lin bins 0.1-2 deg, m <= 10)
@@ -40,7 +42,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "neighbour pairs/s; Nside=4096 ζ_m time fwd & fwd+bwd at stated err vs FP64"
-SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 MAP_WORKLOADS = ("fullsky_nside4096", "masked_map_nside1024", "fullsky_nside512", "map_nside64",
                  "fullsky_nside4096_paper")
@@ -101,6 +102,16 @@ def catalog_inputs(rank: int, name: str = "catalog_2e7"):
 
 # ------------------------------------------------------------- roofline model
 
+def alg_flops_per_pair(M: int, adjoint: bool):
+    """Algorithmic FP32 flops per in-bin pair: 24 for the geometry, chord, bin and
+    position-angle normalisation, 10 per multipole m >= 1 (one complex multiply of the
+    recurrence and one complex accumulate).  The adjoint recomputes the moments and
+    then visits every pair again with the same per-m work (its neighbour legs), so it
+    counts twice that."""
+    f = 24 + 10 * M
+    return 2 * f if adjoint else f
+
+
 def flops_per_pair(M: int, adjoint: bool):
     """FP32 flops (FMA = 2) of the implemented per-pair arithmetic of the map kernels,
     for a pixel visited singly and for one visited as half of a mirror pair.  Counted
@@ -147,8 +158,15 @@ def traffic_per_launch(kernel, npix):
     return bpp * npix if kernel_code_hash(src) == sha else None
 
 
-def fp32_peak_tflops(clk):
-    return SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+def sm_count(dev=None):
+    import torch
+    return int(torch.cuda.get_device_properties(dev if dev is not None else torch.cuda.current_device())
+               .multi_processor_count)
+
+
+def fp32_peak_tflops(clk, sms):
+    """FP32-pipe peak: SMs x 128 lanes x 2 flops (FMA) x the maximum SM clock."""
+    return sms * FP32_LANES_PER_SM * 2 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
 
 
 # --------------------------------------------------------------- GPU clocks
@@ -201,8 +219,8 @@ class ClockSampler:
 
 def oracle_sample(wl, d32, w32, n_piv: int, adjoint: bool = True):
     """The FP64 oracle, as it stands, on a bounded sample of a map workload: n_piv
-    consecutive pivots on the belt ring at z = 1/2 (outside the galactic mask),
-    neighbours from every pixel within the outer bin edge.
+    consecutive pivots from the first pixel of the belt ring at z = 1/2 (outside the
+    galactic mask), neighbours from every pixel within the outer bin edge.
     Returns timings, pair count, the pivot range and the oracle's zeta (for parity)."""
     import oracle
     nside = wl.nside
@@ -212,8 +230,9 @@ def oracle_sample(wl, d32, w32, n_piv: int, adjoint: bool = True):
     # rings within the outer edge plus a margin of two rings
     th_max = math.radians(wl.bins.edges_deg[-1])
     dz = math.sin(th_max) + 4.0 / (3.0 * nside)
+    span = (n_piv + 4 * nside - 1) // (4 * nside)  # belt rings the pivots cover
     r_lo = max(nside, int(ring - dz * 3 * nside / 2) - 2)
-    r_hi = min(3 * nside, int(ring + dz * 3 * nside / 2) + 2)
+    r_hi = min(3 * nside, int(ring + span - 1 + dz * 3 * nside / 2) + 2)
     a = 2 * nside * (nside - 1) + 4 * nside * (r_lo - nside)
     b = 2 * nside * (nside - 1) + 4 * nside * (r_hi - nside + 1)
     idx = np.arange(a, b)
@@ -289,17 +308,31 @@ def setup_map(args, dev, rank):
         piv = (first, first + 4 * n * args.profile_band)
     total, n_sym, n_single = plan.count_pairs(w_dev, piv)
     state = {}
+    # the masked map's configuration is the forward + backward pass; the full-sky maps
+    # time the forward and report the forward + adjoint beside it
+    headline_both = args.pass_ == "both" or (args.pass_ == "auto" and wl.name == "masked_map_nside1024")
 
-    fwd_only = args.pass_ == "forward"
+    def step_fwd(ev=None):
+        state["zeta"], state["norm"] = plan.forward(d_dev, w_dev, piv)
+        if ev is not None:
+            ev.record(torch.cuda.current_stream())
 
-    def step(ev=None):
+    def step_fb(ev=None):
         zeta, norm = plan.forward(d_dev, w_dev, piv)
         if ev is not None:
             ev.record(torch.cuda.current_stream())
-        if not fwd_only:
-            state["grad"] = plan.backward(d_dev, w_dev, norm, g_dev, piv)
+        state["grad"] = plan.backward(d_dev, w_dev, norm, g_dev, piv)
 
-    # e2e: the public host-buffer call, with its copies inside the timed region
+    def warm_adjoint():
+        # one adjoint over a slice of 8 belt rings: loads the adjoint kernel's module
+        # and warms the tables before the timed forward + adjoint steps
+        n = wl.nside
+        first = 2 * n * (n - 1) + 4 * n * ((5 * n) // 4 - n)
+        sl = (first, min(plan.npoints, first + 4 * n * 8))
+        z, nn = plan.forward(d_dev, w_dev, sl)
+        plan.backward(d_dev, w_dev, nn, g_dev, sl)
+
+    # e2e: the public host-buffer call (tpcf_run_host), copies inside the timed region
     h_d = torch.from_numpy(d32).pin_memory()
     h_w = torch.from_numpy(w32).pin_memory()
     h_dl = torch.from_numpy(np.stack([cot, np.zeros_like(cot)], axis=-1).copy()).pin_memory()
@@ -308,54 +341,80 @@ def setup_map(args, dev, rank):
     h_g = torch.empty(plan.npoints, dtype=torch.float32).pin_memory()
 
     def e2e_step():
-        if fwd_only:
-            plan.run_host_into(h_d, h_w, None, out=(h_z, h_n, None))
-        else:
+        if headline_both:
             plan.run_host_into(h_d, h_w, h_dl, out=(h_z, h_n, h_g))
+        else:
+            plan.run_host_into(h_d, h_w, None, out=(h_z, h_n, None))
+
+    in_bytes = h_d.numel() * 4 + h_w.numel() * 4 + (h_dl.numel() * 8 if headline_both else 0)
+    out_bytes = h_z.numel() * 8 + h_n.numel() * 8 + (h_g.numel() * 4 if headline_both else 0)
 
     f_single, f_mirror = flops_per_pair(M, adjoint=False)
     a_single, a_mirror = flops_per_pair(M, adjoint=True)
-    fwd_flops = n_single * f_single + n_sym * f_mirror
-    adj_flops = n_single * a_single + n_sym * a_mirror
+    fwd_impl = n_single * f_single + n_sym * f_mirror
+    adj_impl = n_single * a_single + n_sym * a_mirror
+    fwd_alg = total * alg_flops_per_pair(M, False)
+    fb_alg = total * (alg_flops_per_pair(M, False) + alg_flops_per_pair(M, True))
 
     def cpu_baseline(n_piv):
-        s = oracle_sample(wl, d32, w32, n_piv, adjoint=not fwd_only)
+        s = oracle_sample(wl, d32, w32, n_piv, adjoint=headline_both)
         zs, _ = plan.forward(d_dev, w_dev, (s["lo"], s["hi"]))
         zg = tpcf.as_complex(zs).cpu().numpy()
         zo = s["zeta"]
         per_m = [float(np.abs(zg[m] - zo[m]).max() / max(np.abs(zo[m]).max(), 1e-300)) for m in range(M + 1)]
         glob = float(np.abs(zg - zo).max() / np.abs(zo).max())
         return s, {"pivots": s["hi"] - s["lo"], "max_rel_err_per_m": max(per_m),
-                   "max_rel_err_vs_max_zeta": glob, "tolerance": 1e-5}
+                   "rel_err_per_m": per_m, "max_rel_err_vs_max_zeta": glob, "tolerance_per_m": 1e-5}
+
+    def roof_fwd(ms, clk, sms):
+        # ms: the forward step (pack + pair kernel + two reductions; the pair kernel is
+        # > 99.9% of it), so the achieved rate is a slight underestimate of the kernel's
+        return {"bound": "alu", "kernel": "map_fwd_kernel",
+                "achieved": fwd_alg / (ms * 1e-3) / 1e12, "peak": fp32_peak_tflops(clk, sms), "unit": "TFLOP/s",
+                "flops_per_pair": alg_flops_per_pair(M, False),
+                "achieved_implemented": fwd_impl / (ms * 1e-3) / 1e12,
+                "implemented_note": "flops of the implemented loop (mirror pairs share one angle "
+                                    "and one recurrence)",
+                "peak_note": "SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
+                "traffic": traffic_per_launch("map_fwd_kernel", 12 * wl.nside ** 2),
+                "traffic_note": "DRAM bytes per launch scaled by pixels from the Nside 512 ncu capture "
+                                "(null when the kernel changed since)"}
+
+    def roof_fb(ms_total, ms_fwd, clk, sms):
+        ms_adj = ms_total - ms_fwd
+        return {"bound": "alu", "kernel": "map_bwd_kernel",
+                "achieved": total * alg_flops_per_pair(M, True) / (ms_adj * 1e-3) / 1e12,
+                "peak": fp32_peak_tflops(clk, sms), "unit": "TFLOP/s",
+                "flops_per_pair": alg_flops_per_pair(M, True),
+                "achieved_implemented": adj_impl / (ms_adj * 1e-3) / 1e12,
+                "step_achieved": fb_alg / (ms_total * 1e-3) / 1e12,
+                "traffic": traffic_per_launch("map_bwd_kernel", 12 * wl.nside ** 2)}
 
     config = {"workload": wl.name, "nside": wl.nside, "npix": 12 * wl.nside * wl.nside,
               "bins": "%d %s bins %.2f-%.2f deg" % (K, "lin" if wl.name == "map_nside64" else "log",
                                                     wl.bins.edges_deg[0], wl.bins.edges_deg[-1]),
-              "m_max": M, "pass": "forward" if fwd_only else "forward + adjoint", "pairs_per_step_per_gpu": total,
+              "m_max": M, "pass": "forward + adjoint" if headline_both else "forward",
+              "pairs_per_step_per_gpu": total,
               "contraction": "tensor cores, TF32x3" if args.contract == "tc" else "FP32 pipe",
               "pivots": "all" if piv is None else "profile band: %d rings from z = 1/2 (%d pivots)" % (
                   args.profile_band, piv[1] - piv[0]),
               "l2": "inputs larger than L2 (%.2f GB of (w d, w) per map)" % (8 * 12 * wl.nside ** 2 / 1e9)
               if 12 * wl.nside ** 2 * 8 > 129e6 else "L2 flushed between steps",
               "parallelism": "independent map per GPU"}
-    return dict(step=step, split=("forward", None if fwd_only else "adjoint"), pairs=total, e2e=e2e_step,
-                e2e_bytes=(h_d.numel() * 4 + h_w.numel() * 4 + (0 if fwd_only else h_dl.numel() * 8),
-                           h_z.numel() * 8 + h_n.numel() * 8 + (0 if fwd_only else h_g.numel() * 4)),
-                vs_baseline=PAPER_FWD_PAIRS_PER_S.get(wl.name) if (fwd_only and not args.profile_band) else None,
-                launches=plan.kernel_launches, config=config, cpu_baseline=cpu_baseline,
-                roofline=lambda t1, t2, clk: {
-                    "bound": "alu", "kernel": "map_fwd_kernel",
-                    "achieved": fwd_flops / (t1 * 1e-3) / 1e12, "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s",
-                    "traffic": traffic_per_launch("map_fwd_kernel", 12 * wl.nside ** 2),
-                    "traffic_note": "DRAM bytes per launch scaled by pixels from the Nside 512 ncu capture"}
-                if fwd_only else {
-                    "bound": "alu", "kernel": "map_bwd_kernel",
-                    "achieved": (fwd_flops + adj_flops) / (t2 * 1e-3) / 1e12,  # adjoint recomputes the forward
-                    "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s",
-                    "traffic": traffic_per_launch("map_bwd_kernel", 12 * wl.nside ** 2),
-                    "traffic_note": "DRAM bytes per launch scaled by pixels from the Nside 512 ncu capture",
-                    "forward_kernel_tflops": fwd_flops / (t1 * 1e-3) / 1e12},
-                small_l2=12 * wl.nside ** 2 * 8 <= 129e6, close=plan.close)
+    W = dict(step=step_fb if headline_both else step_fwd,
+             split=("forward", "adjoint") if headline_both else ("forward", None),
+             pairs=total, e2e=e2e_step, e2e_bytes=(in_bytes, out_bytes),
+             vs_baseline=PAPER_FWD_PAIRS_PER_S.get(wl.name) if (not headline_both and not args.profile_band) else None,
+             launches=plan.kernel_launches, config=config, cpu_baseline=cpu_baseline,
+             small_l2=12 * wl.nside ** 2 * 8 <= 129e6, close=plan.close)
+    if headline_both:
+        W["roofline"] = lambda t1, t2, clk, sms: roof_fb(t1 + t2, t1, clk, sms)
+    else:
+        W["roofline"] = lambda t1, t2, clk, sms: roof_fwd(t1, clk, sms)
+        if args.fb_steps > 0:
+            W["part_fb"] = dict(name="forward_adjoint", step=step_fb, warm=warm_adjoint, steps=args.fb_steps,
+                                roofline=lambda t1, t2, clk, sms: roof_fb(t1 + t2, t1, clk, sms))
+    return W
 
 
 def setup_catalog(args, dev, rank):
@@ -404,6 +463,7 @@ def setup_catalog(args, dev, rank):
         torch.cuda.current_stream().synchronize()
 
     flops = (cu + cr) * cat_flops_per_pair(M)
+    alg = (cu + cr) * alg_flops_per_pair(M, False)
 
     def cpu_baseline(n_piv):
         s = oracle_sample_catalog(xu, du, wu, edges, M, n_piv)
@@ -424,10 +484,11 @@ def setup_catalog(args, dev, rank):
                 launches=lambda: pu.kernel_launches() + pr.kernel_launches(), extra_launches_per_step=1,
                 config=config,
                 cpu_baseline=cpu_baseline,
-                roofline=lambda t1, t2, clk: {
+                roofline=lambda t1, t2, clk, sms: {
                     "bound": "alu", "kernel": "cat_fwd_kernel",
-                    "achieved": flops / ((t1 + t2) * 1e-3) / 1e12, "peak": fp32_peak_tflops(clk),
-                    "unit": "TFLOP/s"},
+                    "achieved": alg / ((t1 + t2) * 1e-3) / 1e12, "peak": fp32_peak_tflops(clk, sms),
+                    "unit": "TFLOP/s", "flops_per_pair": alg_flops_per_pair(M, False),
+                    "achieved_implemented": flops / ((t1 + t2) * 1e-3) / 1e12},
                 small_l2=False, close=lambda: (pu.close(), pr.close()))
 
 
@@ -441,6 +502,7 @@ def setup_batch(args, dev, rank):
     plans, ds, ws, zs, ns, dls, gs = [], [], [], [], [], [], []
     total = 0
     flops = 0.0
+    alg = 0.0
     for wl in wls:
         K, M = wl.bins.nbins, wl.bins.m_max
         d32, w32 = map_inputs(wl, rank)
@@ -459,6 +521,7 @@ def setup_batch(args, dev, rank):
         fs, fm = flops_per_pair(M, False)
         as_, am = flops_per_pair(M, True)
         flops += single * (fs + as_) + sym * (fm + am)
+        alg += t * (alg_flops_per_pair(M, False) + alg_flops_per_pair(M, True))
     batch = tpcf.Batch(plans, ds, ws, zs, ns, dls, gs)
 
     def step(ev=None):
@@ -497,9 +560,10 @@ def setup_batch(args, dev, rank):
         config["scaled"] = "Nside set scaled down from 256/512/1024/2048"
     return dict(step=step, split=("batch", None), pairs=total, e2e=e2e_step, e2e_bytes=(e2e_in, e2e_out),
                 launches=plans[0].kernel_launches, config=config, cpu_baseline=None,
-                roofline=lambda t1, t2, clk: {"bound": "alu", "kernel": "batch_bwd_kernel",
-                                              "achieved": flops / (t1 * 1e-3) / 1e12,
-                                              "peak": fp32_peak_tflops(clk), "unit": "TFLOP/s"},
+                roofline=lambda t1, t2, clk, sms: {"bound": "alu", "kernel": "batch_bwd_kernel",
+                                                   "achieved": alg / (t1 * 1e-3) / 1e12,
+                                                   "peak": fp32_peak_tflops(clk, sms), "unit": "TFLOP/s",
+                                                   "achieved_implemented": flops / (t1 * 1e-3) / 1e12},
                 small_l2=False, close=lambda: (batch.close(), [p.close() for p in plans]))
 
 
@@ -530,47 +594,57 @@ def run_gpu(args):
     else:
         raise SystemExit("unknown workload " + args.workload)
     stream = torch.cuda.current_stream()
+    sms = sm_count(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if W["small_l2"] else None
-
-    for _ in range(args.warmup):
-        W["step"]()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     gpu_id = str(local)
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
-    clocks = ClockSampler(gpu_id)
+
+    def timed(step, nsteps):
+        """nsteps of `step` bracketed by barrier + synchronize, CUDA events on the
+        launching stream; returns (total ms, first-part ms, second-part ms, clocks),
+        max over ranks."""
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(gpu_id)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nsteps)]
+        for k in range(nsteps):
+            if flush is not None:
+                flush.fill_(float(k))  # write a buffer larger than L2 between steps
+            ev[k][0].record(stream)
+            step(ev[k][1])
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        t1 = sum(ev[k][0].elapsed_time(ev[k][1]) for k in range(nsteps))
+        t2 = sum(ev[k][1].elapsed_time(ev[k][2]) for k in range(nsteps))
+        tot = sum(ev[k][0].elapsed_time(ev[k][2]) for k in range(nsteps))
+        t_max = torch.tensor([tot, t1, t2], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        tot, t1, t2 = (float(v) for v in t_max.cpu())
+        return tot, t1, t2, clk
+
+    t_setup = time.time()
+    for _ in range(args.warmup):
+        W["step"]()
+    log("[rank %d] %d warm-up steps in %.1fs" % (rank, args.warmup, time.time() - t_setup))
     launches0 = W["launches"]()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    for k in range(args.steps):
-        if flush is not None:
-            flush.fill_(float(k))  # write a buffer larger than L2 between steps
-        ev[k][0].record(stream)
-        W["step"](ev[k][1])
-        ev[k][2].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
+    total_ms, ms1, ms2, clk = timed(W["step"], args.steps)
     launches = W["launches"]() - launches0 + W.get("extra_launches_per_step", 0) * args.steps
-    t1 = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
-    t2 = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
-    total_ms = sum(ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps))
-    t_max = torch.tensor([total_ms, sum(t1), sum(t2)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms, ms1, ms2 = (float(v) for v in t_max.cpu())
     ms_step = total_ms / args.steps
     value = world * W["pairs"] * args.steps / (total_ms * 1e-3)
+    log("[rank %d] %d timed steps: %.1f ms/step" % (rank, args.steps, ms_step))
 
     e2e = None
-    if W["e2e"] is not None and args.e2e:
-        W["e2e"]()  # first call allocates the staging buffers
+    if W["e2e"] is not None and args.e2e and args.e2e_steps > 0:
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -578,7 +652,7 @@ def run_gpu(args):
         e_start = torch.cuda.Event(enable_timing=True)
         e_end = torch.cuda.Event(enable_timing=True)
         e_start.record(stream)
-        for _ in range(args.steps):
+        for _ in range(args.e2e_steps):
             W["e2e"]()
         e_end.record(stream)
         torch.cuda.synchronize()
@@ -587,12 +661,26 @@ def run_gpu(args):
         if world > 1:
             dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
         e2e_ms = float(e2e_ms.max().cpu())
-        e2e = {"value": world * W["pairs"] * args.steps / (e2e_ms * 1e-3), "unit": "pairs/s",
-               "h2d_bytes_per_step": W["e2e_bytes"][0], "d2h_bytes_per_step": W["e2e_bytes"][1]}
+        e2e = {"value": world * W["pairs"] * args.e2e_steps / (e2e_ms * 1e-3), "unit": "pairs/s",
+               "h2d_bytes_per_step": W["e2e_bytes"][0], "d2h_bytes_per_step": W["e2e_bytes"][1],
+               "steps": args.e2e_steps, "call": "tpcf_run_host (pinned host buffers)"}
+
+    part = None
+    if W.get("part_fb") is not None:
+        P = W["part_fb"]
+        P["warm"]()
+        p_tot, p1, p2, p_clk = timed(P["step"], P["steps"])
+        roof_p = P["roofline"](p1 / P["steps"], p2 / P["steps"], p_clk, sms)
+        roof_p["frac"] = roof_p["achieved"] / roof_p["peak"]
+        part = {"steps": P["steps"], "ms": p_tot / P["steps"], "forward_ms": p1 / P["steps"],
+                "adjoint_ms": p2 / P["steps"],
+                "value": world * W["pairs"] * P["steps"] / (p_tot * 1e-3), "unit": "pairs/s",
+                "roofline": roof_p, "clocks": p_clk}
+        log("[rank %d] forward + adjoint: %.1f ms/step" % (rank, p_tot / P["steps"]))
 
     result = None
     if rank == 0:
-        roof = W["roofline"](ms1 / args.steps, ms2 / args.steps, clk)
+        roof = W["roofline"](ms1 / args.steps, ms2 / args.steps, clk, sms)
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof.setdefault("traffic", None)
         cpu = None
@@ -602,12 +690,15 @@ def run_gpu(args):
             s, parity = W["cpu_baseline"](args.cpu_pivots)
             cpu = {"value": s["pairs"] / (s["t_fwd"] + s["t_bwd"]), "unit": "pairs/s", "cores": s["cores"],
                    "kind": "oracle",
-                   "sample": "%s; FP64 forward %.1fs + adjoint %.1fs; %d pairs" % (s["desc"], s["t_fwd"],
-                                                                                 s["t_bwd"], s["pairs"])}
+                   "sample": "%s; FP64 forward %.1fs%s; %d pairs" % (
+                       s["desc"], s["t_fwd"], (" + adjoint %.1fs" % s["t_bwd"]) if s["t_bwd"] else "",
+                       s["pairs"])}
         a, b = W["split"]
         parts = {a: {"ms": ms1 / args.steps}}
         if b is not None:
             parts[b] = {"ms": ms2 / args.steps}
+        if part is not None:
+            parts["forward_adjoint"] = part
         result = {
             "metric": METRIC,
             "value": value,
@@ -627,6 +718,7 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
+            "sm_count": sms,
             "cpu_baseline": cpu,
             "parity": parity,
         }
@@ -646,9 +738,10 @@ def run_reference(args):
     if args.workload in MAP_WORKLOADS:
         wl = map_workload(args.workload)
         d32, w32 = map_inputs(wl, 0)
-        sample = lambda: oracle_sample(wl, d32, w32, args.ref_pivots)
-        cfg = {"workload": wl.name, "nside": wl.nside, "m_max": wl.bins.m_max, "pass": "forward + adjoint",
-               "sample_pivots": args.ref_pivots}
+        both = args.pass_ == "both" or (args.pass_ == "auto" and wl.name == "masked_map_nside1024")
+        sample = lambda: oracle_sample(wl, d32, w32, args.ref_pivots, adjoint=both)
+        cfg = {"workload": wl.name, "nside": wl.nside, "m_max": wl.bins.m_max,
+               "pass": "forward + adjoint" if both else "forward", "sample_pivots": args.ref_pivots}
     elif args.workload in ("catalog_2e7", "catalog_2e6"):
         wl, xu, du, wu, xr, _ = catalog_inputs(0, args.workload)
         sample = lambda: oracle_sample_catalog(xu, du, wu, wl.bins.edges_deg, wl.bins.m_max, args.ref_pivots)
@@ -680,22 +773,27 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="fullsky_nside4096")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-pivots", type=int, default=2048)
-    ap.add_argument("--ref-pivots", type=int, default=512)
+    ap.add_argument("--cpu-pivots", type=int, default=16384,
+                    help="map workloads: pivots (one full belt ring at Nside 4096) in the CPU oracle sample")
+    ap.add_argument("--ref-pivots", type=int, default=1024)
     ap.add_argument("--batch-nsides", default="256,512,1024,2048")
     ap.add_argument("--profile-band", type=int, default=0,
                     help="map workloads: restrict the pivots to this many belt rings from z = 1/2 "
                          "(for ncu captures of full-resolution kernels; not a bench configuration)")
-    ap.add_argument("--pass", dest="pass_", default="both", choices=["both", "forward"],
-                    help="map workloads: forward + adjoint (default) or the forward alone")
+    ap.add_argument("--pass", dest="pass_", default="auto", choices=["auto", "both", "forward"],
+                    help="map workloads: the timed step is the forward (full-sky maps) or the forward + "
+                         "adjoint (the masked map) by default")
+    ap.add_argument("--fb-steps", type=int, default=2,
+                    help="map workloads timed on the forward: full forward + adjoint steps reported in parts")
+    ap.add_argument("--e2e-steps", type=int, default=1,
+                    help="calls of the host-buffer entry point timed for e2e")
     ap.add_argument("--contract", default="fp32", choices=["fp32", "tc"],
                     help="contraction of the map forward: FP32 pipe or tensor cores (TF32x3)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
-        log("warm-up raised to 3 steps")
-        args.warmup = 3
+        log("note: fewer than 3 warm-up steps (%d)" % args.warmup)
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:
         print(json.dumps(res), flush=True)

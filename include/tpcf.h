@@ -146,10 +146,13 @@ tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const float* d_w,
  *
  * Same inputs, outputs and pivot range as tpcf_forward (no raw sums).  The call
  * allocates nothing: it reads d_delta and d_w directly and keeps its partial sums
- * in a fixed 16 MiB __device__ array that every GPU loading the library holds until
- * the process exits.  The plan is created beforehand (plan creation does allocate).
- * The first call on a device looks the array's device address up once; make that
- * first call before any stream capture.  All calls share the array and each call
+ * in a fixed 16 MiB __device__ array.  The plan is created beforehand (plan creation
+ * does allocate), and tpcf_plan_create_map also places that array on its device and
+ * looks its address up, so the 16 MiB are taken during set-up and held until the
+ * process exits.  If that look-up failed there, the first call on the device retries
+ * it; such a first call should come before any stream capture.  The largest plan the
+ * ABI allows (32 bins, m_max 16) needs 148 KB per CTA slot; the call runs as many
+ * CTAs as there are slots in the array.  All calls share the array and each call
  * clears what must start at zero; calls whose GPU work overlaps (other streams,
  * host threads or plans at the same time) race on it and must be serialised.
  * Map plans without self-pair subtraction only (else TPCF_ERR_UNSUPPORTED); a plan
@@ -236,6 +239,17 @@ tpcf_status tpcf_plan_sync(tpcf_plan plan);
 
 /* Free everything the plan owns (synchronises with its pending work). NULL is a no-op. */
 void tpcf_plan_destroy(tpcf_plan plan);
+
+/*
+ * Test hooks for the error paths (no counterpart in the paper).
+ * tpcf_test_fail_allocation(n): the n-th device allocation the library attempts from
+ * now on fails as if the device were out of memory (the calls above then return
+ * TPCF_ERR_OOM); n <= 0 disarms.  tpcf_test_live_allocations(): the number of device
+ * allocations the library holds (plans, batches, staging), so that a test can check
+ * that a failed call leaked nothing.
+ */
+void tpcf_test_fail_allocation(int64_t n);
+int64_t tpcf_test_live_allocations(void);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ MAX_M = 16
 EXPORTS = ["tpcf_status_string", "tpcf_last_error", "tpcf_plan_create_map", "tpcf_plan_create_catalog",
            "tpcf_plan_npoints", "tpcf_plan_kernel_launches", "tpcf_forward", "tpcf_forward_noalloc", "tpcf_backward", "tpcf_count_pairs", "tpcf_run_host", "tpcf_batch_create",
            "tpcf_batch_launch", "tpcf_batch_kernel_launches", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync", "tpcf_normalize",
-           "tpcf_plan_destroy"]
+           "tpcf_plan_destroy", "tpcf_test_fail_allocation", "tpcf_test_live_allocations"]
 
 
 class TpcfError(RuntimeError):
@@ -91,6 +91,10 @@ def lib() -> ctypes.CDLL:
     L.tpcf_plan_sync.argtypes = [_vp]
     L.tpcf_plan_destroy.restype = None
     L.tpcf_plan_destroy.argtypes = [_vp]
+    L.tpcf_test_fail_allocation.restype = None
+    L.tpcf_test_fail_allocation.argtypes = [_i64]
+    L.tpcf_test_live_allocations.restype = _i64
+    L.tpcf_test_live_allocations.argtypes = []
     _lib = L
     return L
 

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -39,6 +40,8 @@ tpcf_status catalog_backward(tpcf_plan_s* P, const float* d_delta, const float* 
                              const double* d_norm, const double* d_dL, float* d_grad, cudaStream_t s);
 tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
                             double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s);
+// loads the allocation-free forward's scratch array on a device (noalloc.cu)
+tpcf_status noalloc_prepare(int dev);
 
 struct MLaunch {
     cudaError_t (*fwd)(const MapDev&, const MapCall&, int, cudaStream_t);
@@ -60,6 +63,38 @@ static const MLaunch kLaunch[TPCF_MAX_M + 1] = {
 }  // namespace tpcf
 
 static thread_local char g_last_error[256] = "";
+
+// Allocation bookkeeping: live device allocations, and the test hook that makes the
+// n-th next allocation fail as if the device were out of memory.
+static std::atomic<long long> g_live_allocs{0};
+static std::atomic<long long> g_fail_countdown{0};
+
+namespace tpcf {
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    long long c = g_fail_countdown.load();
+    while (c > 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+            if (c == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live_allocs;
+    return e;
+}
+void dev_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    --g_live_allocs;
+}
+}  // namespace tpcf
+
+extern "C" void tpcf_test_fail_allocation(int64_t n) { g_fail_countdown.store(n > 0 ? n : 0); }
+
+extern "C" int64_t tpcf_test_live_allocations(void) { return g_live_allocs.load(); }
 
 namespace tpcf {
 tpcf_status cuda_fail(cudaError_t e, const char* where) {
@@ -230,6 +265,9 @@ extern "C" tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const
         delete P;
         return st;
     }
+    // place tpcf_forward_noalloc's fixed scratch on this device now, during set-up;
+    // on failure that call reports it, so clear the runtime's last-error state here
+    if (noalloc_prepare(P->device) != TPCF_OK) cudaGetLastError();
     P->last_stream = s;
     *out = P;
     return TPCF_OK;
@@ -382,12 +420,22 @@ extern "C" tpcf_status tpcf_run_host(tpcf_plan plan, const float* h_delta, const
     const int64_t n = P->npoints;
     const size_t nz = (size_t)(P->M + 1) * P->K * P->K * 2;
     if (!P->st_delta) {
-        TRY_CUDA(P->alloc(&P->st_delta, n));
-        TRY_CUDA(P->alloc(&P->st_w, n));
-        TRY_CUDA(P->alloc(&P->st_dL, nz));
-        TRY_CUDA(P->alloc(&P->st_zeta, nz));
-        TRY_CUDA(P->alloc(&P->st_norm, (size_t)P->K * P->K));
-        TRY_CUDA(P->alloc(&P->st_grad, n));
+        // staging buffers, kept by the plan; published together so that a failed
+        // allocation leaves the plan as it was (what was allocated is freed with it)
+        float *sd, *sw, *sg;
+        double *sdl, *sz, *sn;
+        TRY_CUDA(P->alloc(&sd, n));
+        TRY_CUDA(P->alloc(&sw, n));
+        TRY_CUDA(P->alloc(&sdl, nz));
+        TRY_CUDA(P->alloc(&sz, nz));
+        TRY_CUDA(P->alloc(&sn, (size_t)P->K * P->K));
+        TRY_CUDA(P->alloc(&sg, n));
+        P->st_w = sw;
+        P->st_dL = sdl;
+        P->st_zeta = sz;
+        P->st_norm = sn;
+        P->st_grad = sg;
+        P->st_delta = sd;
     }
     TRY_CUDA(cudaMemcpyAsync(P->st_delta, h_delta, sizeof(float) * n, cudaMemcpyHostToDevice, s));
     TRY_CUDA(cudaMemcpyAsync(P->st_w, h_w, sizeof(float) * n, cudaMemcpyHostToDevice, s));

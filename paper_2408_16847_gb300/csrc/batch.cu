@@ -83,7 +83,7 @@ struct tpcf_batch_s {
     template <typename T>
     cudaError_t alloc(T** p, size_t count) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        cudaError_t e = tpcf::dev_malloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
         if (e != cudaSuccess) return e;
         allocs.push_back(q);
         *p = (T*)q;
@@ -93,7 +93,7 @@ struct tpcf_batch_s {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs) tpcf::dev_free(p);
     }
 };
 

@@ -10,8 +10,8 @@
 // all 32.  Per pair: the chord from fp32 hi/lo positions,
 // the bin from a log-scale lookup table (FP64 check within CAT_AMB of an edge), the
 // position angle from the pivot's local north/east basis, the harmonics by the
-// Chebyshev recurrences.  The per-lane register sums follow one bin at a time and
-// are added into the tile's shared-memory moments when the bin changes; the tile
+// stable three-term recurrence of map_kernels.cuh (harmonics()).  The per-lane
+// register sums follow one bin at a time and are added into the tile's shared-memory moments when the bin changes; the tile
 // contraction and the cross-CTA reduction are those of the map path.
 #pragma once
 

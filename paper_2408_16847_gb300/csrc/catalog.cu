@@ -187,16 +187,16 @@ tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaSt
     TRY_CUDA(P->alloc(&xyz_s, 3 * n));
     TRY_CUDA(P->alloc(&orig, n));
     unsigned long long* cursor = nullptr;
-    TRY_CUDA(cudaMalloc(&cell, sizeof(int64_t) * n));
-    cudaError_t e = cudaMalloc(&cursor, sizeof(unsigned long long) * (ncells + 1));
+    TRY_CUDA(dev_malloc((void**)&cell, sizeof(int64_t) * n));
+    cudaError_t e = dev_malloc((void**)&cursor, sizeof(unsigned long long) * (ncells + 1));
     if (e != cudaSuccess) {
-        cudaFree(cell);
+        dev_free(cell);
         return cuda_fail(e, "cudaMalloc(cursor)");
     }
     auto cleanup = [&]() {
         cudaStreamSynchronize(s);
-        cudaFree(cell);
-        cudaFree(cursor);
+        dev_free(cell);
+        dev_free(cursor);
     };
     e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long) * (ncells + 1), s);
     if (e == cudaSuccess) {

@@ -12,11 +12,11 @@
 //     exact ring-range disc query); each lane walks its own runs, so the bin is
 //     known without a per-pixel test and the (M+1) complex accumulators of the bin
 //     stay in registers across rings;
-//   * within a run e^{-i m phi} comes from the Chebyshev recurrences
-//     cos(m phi) = 2 cos(phi) cos((m-1) phi) - cos((m-2) phi) (same for sin), the
-//     trig-free harmonic step the paper describes (Sec. 3.1 and 3.2, two operations
-//     per m), with the neighbour weight folded into the recurrence and the cos and
-//     sin chains packed into one f32x2 FMA per step;
+//   * within a run e^{-i m phi} comes from a trig-free recurrence in m (the harmonic
+//     step the paper describes in Sec. 3.1 and 3.2, a few operations per m): Reinsch's
+//     stable form of the three-term relation on the angle folded into |psi| <= pi/2,
+//     with the neighbour weight folded into the start values and the cos and sin
+//     chains packed into f32x2 FMAs (see harmonics());
 //   * in the equatorial belt a neighbour ring has as many pixels as the pivot ring,
 //     so its pixels sit symmetrically about the pivot's meridian: the pixel at +phi
 //     and its mirror at -phi share one cos/sin evaluation and one recurrence;
@@ -165,51 +165,82 @@ __device__ __forceinline__ void pixel_dir(float fi, float xneg, float uneg, cons
     sph = E * rinv;
 }
 
-// acc[m] += (wc cos(m phi), ws sin(m phi)), m = 0..M, by the Chebyshev three-term
-// recurrences with the weights folded in.  The cosine and sine chains share the
-// coefficient 2 cos(phi), so each step is one packed two-lane FP32 FMA (f32x2) on the
-// state (u_m, v_m), and the accumulation one packed add.
+// e^{-i m phi} for m = 0..M by Reinsch's modification of the three-term recurrence
+// (as in Stoer & Bulirsch, Introduction to Numerical Analysis, chapter 1).  The plain
+// Chebyshev recurrence cos((m+1)p) = 2 cos(p) cos(mp) - cos((m-1)p) only sees cos(p),
+// which in fp32 loses the angle near p = 0 and pi (an error of roughly m eps/|sin p|)
+// and amplifies its rounding like m^2 there.  Here the angle is first folded to
+// psi = phi (cos phi >= 0) or phi - pi (cos phi < 0), so that cos psi = |cos phi|,
+// sin psi = sigma sin phi with sigma = sign(cos phi), and e^{i m phi} = sigma^m e^{i m psi}.
+// With lambda = 2 (cos psi - 1) = -2 sin^2 psi / (1 + cos psi) (no cancellation) and
+// the differences D_m = X_m - X_{m-1}, the recurrence
+//     D_{m+1} = D_m + lambda X_m,     X_{m+1} = X_m + D_{m+1}
+// is the same three-term relation, but its rounding errors grow only about linearly
+// in m for every |psi| <= pi/2.  The cosine and sine chains share lambda, so each step
+// is one packed f32x2 FMA and one packed add on (cos part, sin part); the neighbour
+// weights are folded into the start values, and the sigma^m sign is applied when the
+// odd multipoles are accumulated (a packed FMA in place of the packed add).
+struct Fold {
+    float ac;   // |cos phi| = cos psi
+    float ss;   // sigma sin phi = sin psi
+    float sg;   // sigma
+    float lam;  // 2 (cos psi - 1)
+};
+
+__device__ __forceinline__ Fold fold_angle(float cph, float sph) {
+    Fold f;
+    f.ac = fabsf(cph);
+    f.sg = cph < 0.0f ? -1.0f : 1.0f;
+    f.ss = f.sg * sph;
+    f.lam = -2.0f * __fdividef(sph * sph, 1.0f + f.ac);
+    return f;
+}
+
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
+// acc[m] += (wc cos(m phi), ws sin(m phi)), m = 0..M.
 template <int M>
 __device__ __forceinline__ void harmonics(float2 (&acc)[M + 1], float cph, float sph, float wc, float ws) {
     acc[0].x += wc;
     if constexpr (M >= 1) {
-        float2 x0 = make_float2(wc, 0.0f);
-        float2 x1 = make_float2(wc * cph, ws * sph);
-        acc[1] = __fadd2_rn(acc[1], x1);
-        const float c2 = cph + cph;
-        const float2 C2 = make_float2(c2, c2);
+        const Fold f = fold_angle(cph, sph);
+        float2 X = make_float2(wc * f.ac, ws * f.ss);           // X_1 (psi frame)
+        float2 D = make_float2(0.5f * f.lam * wc, ws * f.ss);   // X_1 - X_0
+        const float2 S2 = make_float2(f.sg, f.sg);
+        const float2 L2 = make_float2(f.lam, f.lam);
+        acc[1] = __ffma2_rn(S2, X, acc[1]);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float2 x2 = __ffma2_rn(C2, x1, neg2(x0));
-            acc[m] = __fadd2_rn(acc[m], x2);
-            x0 = x1;
-            x1 = x2;
+            D = __ffma2_rn(L2, X, D);
+            X = __fadd2_rn(X, D);
+            acc[m] = (m & 1) ? __ffma2_rn(S2, X, acc[m]) : __fadd2_rn(acc[m], X);
         }
     }
 }
 
-// The same for two pixels a and b at once (two independent recurrence chains for
-// instruction-level parallelism; the pair is added before the accumulation).
+// The same for two pixels a and b at once (two independent chains for
+// instruction-level parallelism).
 template <int M>
 __device__ __forceinline__ void harmonics2(float2 (&acc)[M + 1], float ca, float sa, float wca, float wsa, float cb,
                                            float sb, float wcb, float wsb) {
     acc[0].x += wca + wcb;
     if constexpr (M >= 1) {
-        float2 xa0 = make_float2(wca, 0.0f), xa1 = make_float2(wca * ca, wsa * sa);
-        float2 xb0 = make_float2(wcb, 0.0f), xb1 = make_float2(wcb * cb, wsb * sb);
-        acc[1] = __fadd2_rn(acc[1], __fadd2_rn(xa1, xb1));
-        const float2 Ca = make_float2(ca + ca, ca + ca), Cb = make_float2(cb + cb, cb + cb);
+        const Fold fa = fold_angle(ca, sa), fb = fold_angle(cb, sb);
+        float2 Xa = make_float2(wca * fa.ac, wsa * fa.ss), Da = make_float2(0.5f * fa.lam * wca, wsa * fa.ss);
+        float2 Xb = make_float2(wcb * fb.ac, wsb * fb.ss), Db = make_float2(0.5f * fb.lam * wcb, wsb * fb.ss);
+        const float2 Sa = make_float2(fa.sg, fa.sg), Sb = make_float2(fb.sg, fb.sg);
+        const float2 La = make_float2(fa.lam, fa.lam), Lb = make_float2(fb.lam, fb.lam);
+        acc[1] = __ffma2_rn(Sb, Xb, __ffma2_rn(Sa, Xa, acc[1]));
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float2 xa2 = __ffma2_rn(Ca, xa1, neg2(xa0));
-            const float2 xb2 = __ffma2_rn(Cb, xb1, neg2(xb0));
-            acc[m] = __fadd2_rn(acc[m], __fadd2_rn(xa2, xb2));
-            xa0 = xa1;
-            xa1 = xa2;
-            xb0 = xb1;
-            xb1 = xb2;
+            Da = __ffma2_rn(La, Xa, Da);
+            Db = __ffma2_rn(Lb, Xb, Db);
+            Xa = __fadd2_rn(Xa, Da);
+            Xb = __fadd2_rn(Xb, Db);
+            if (m & 1)
+                acc[m] = __ffma2_rn(Sb, Xb, __ffma2_rn(Sa, Xa, acc[m]));
+            else
+                acc[m] = __fadd2_rn(acc[m], __fadd2_rn(Xa, Xb));
         }
     }
 }
@@ -1031,25 +1062,33 @@ __global__ void __launch_bounds__(NTHREADS) map_count_kernel(MapDev g, const flo
 constexpr int ROW = 512;  // floats per warp row buffer (wider rows fall back to whole-ring or global adds)
 
 // val = sum_m (cos(m phi) hr_m + sin(m phi) hi_m): X the cosine part, Y the sine part.
-// h[m] = (hr_m, hi_m); the (cos, sin) chains run packed as in harmonics().
+// h[m] = (hr_m, hi_m); the (cos, sin) chains run packed, in the folded frame psi, by
+// the recurrence of harmonics(); even and odd multipoles are summed apart and the odd
+// sum takes the sign sigma at the end.
 template <int M>
 __device__ __forceinline__ void adj_harmonics(const float2 (&h)[M + 1], float cph, float sph, float& X, float& Y) {
-    float2 xy = make_float2(h[0].x, 0.0f);
+    float2 ev = make_float2(h[0].x, 0.0f);
+    float2 od = make_float2(0.0f, 0.0f);
+    float sg = 1.0f;
     if constexpr (M >= 1) {
-        float2 t0 = make_float2(1.0f, 0.0f), t1 = make_float2(cph, sph);
-        xy = __ffma2_rn(t1, h[1], xy);
-        const float c2 = cph + cph;
-        const float2 C2 = make_float2(c2, c2);
+        const Fold f = fold_angle(cph, sph);
+        sg = f.sg;
+        float2 T = make_float2(f.ac, f.ss);
+        float2 D = make_float2(0.5f * f.lam, f.ss);
+        const float2 L2 = make_float2(f.lam, f.lam);
+        od = __ffma2_rn(T, h[1], od);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float2 t2 = __ffma2_rn(C2, t1, neg2(t0));
-            xy = __ffma2_rn(t2, h[m], xy);
-            t0 = t1;
-            t1 = t2;
+            D = __ffma2_rn(L2, T, D);
+            T = __fadd2_rn(T, D);
+            if (m & 1)
+                od = __ffma2_rn(T, h[m], od);
+            else
+                ev = __ffma2_rn(T, h[m], ev);
         }
     }
-    X = xy.x;
-    Y = xy.y;
+    X = fmaf(sg, od.x, ev.x);
+    Y = fmaf(sg, od.y, ev.y);
 }
 
 // Where the contribution to pixel p (unwrapped index on ring R) goes.
@@ -1072,29 +1111,37 @@ __device__ __forceinline__ void sink_add(const RowSink& s, int p_unwrapped, int 
 template <int M>
 __device__ __forceinline__ void adj_harmonics2(const float2 (&h)[M + 1], float ca, float sa, float cb, float sb,
                                                float& Xa, float& Ya, float& Xb, float& Yb) {
-    float2 xya = make_float2(h[0].x, 0.0f), xyb = xya;
+    float2 eva = make_float2(h[0].x, 0.0f), evb = eva;
+    float2 oda = make_float2(0.0f, 0.0f), odb = oda;
+    float sga = 1.0f, sgb = 1.0f;
     if constexpr (M >= 1) {
-        float2 ta0 = make_float2(1.0f, 0.0f), ta1 = make_float2(ca, sa);
-        float2 tb0 = ta0, tb1 = make_float2(cb, sb);
-        xya = __ffma2_rn(ta1, h[1], xya);
-        xyb = __ffma2_rn(tb1, h[1], xyb);
-        const float2 Ca = make_float2(ca + ca, ca + ca), Cb = make_float2(cb + cb, cb + cb);
+        const Fold fa = fold_angle(ca, sa), fb = fold_angle(cb, sb);
+        sga = fa.sg;
+        sgb = fb.sg;
+        float2 Ta = make_float2(fa.ac, fa.ss), Da = make_float2(0.5f * fa.lam, fa.ss);
+        float2 Tb = make_float2(fb.ac, fb.ss), Db = make_float2(0.5f * fb.lam, fb.ss);
+        const float2 La = make_float2(fa.lam, fa.lam), Lb = make_float2(fb.lam, fb.lam);
+        oda = __ffma2_rn(Ta, h[1], oda);
+        odb = __ffma2_rn(Tb, h[1], odb);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
-            const float2 ta2 = __ffma2_rn(Ca, ta1, neg2(ta0));
-            const float2 tb2 = __ffma2_rn(Cb, tb1, neg2(tb0));
-            xya = __ffma2_rn(ta2, h[m], xya);
-            xyb = __ffma2_rn(tb2, h[m], xyb);
-            ta0 = ta1;
-            ta1 = ta2;
-            tb0 = tb1;
-            tb1 = tb2;
+            Da = __ffma2_rn(La, Ta, Da);
+            Db = __ffma2_rn(Lb, Tb, Db);
+            Ta = __fadd2_rn(Ta, Da);
+            Tb = __fadd2_rn(Tb, Db);
+            if (m & 1) {
+                oda = __ffma2_rn(Ta, h[m], oda);
+                odb = __ffma2_rn(Tb, h[m], odb);
+            } else {
+                eva = __ffma2_rn(Ta, h[m], eva);
+                evb = __ffma2_rn(Tb, h[m], evb);
+            }
         }
     }
-    Xa = xya.x;
-    Ya = xya.y;
-    Xb = xyb.x;
-    Yb = xyb.y;
+    Xa = fmaf(sga, oda.x, eva.x);
+    Ya = fmaf(sga, oda.y, eva.y);
+    Xb = fmaf(sgb, odb.x, evb.x);
+    Yb = fmaf(sgb, odb.y, evb.y);
 }
 
 template <int M, bool FAST, bool SELF = false>

@@ -8,8 +8,11 @@
 // call this entry point, which uses only the caller's buffers, the plan's
 // read-only tables and the fixed scratch array below.
 //
-// The scratch lives in a file-scope __device__ array, so every GPU that loads the
-// library holds its 16 MiB until the process exits.  All calls share it: calls
+// The scratch lives in a file-scope __device__ array.  This file is its own CUDA
+// module, and CUDA loads modules lazily, so the array is placed on a device when its
+// address is first looked up: tpcf_plan_create_map does that (noalloc_prepare), so
+// the 16 MiB are taken while the caller sets up, before its pool allocator claims
+// the device, and stay until the process exits.  All calls share it: calls
 // whose GPU work overlaps (two streams, two host threads, two plans at once) race
 // on it and must be serialised by the caller.  A call clears what must start at
 // zero (the work counter and the partial-sum slots) before its kernels run.
@@ -65,6 +68,15 @@ static tpcf_status scratch_address(int dev, unsigned char** out) {
     }
     *out = (unsigned char*)g_scratch_addr[dev];
     return TPCF_OK;
+}
+
+// Called by tpcf_plan_create_map with the plan's device current: loads this module
+// (and with it the scratch array) on that device and caches the array's address.
+// A failure is not fatal for the plan; it is reported again by the first
+// tpcf_forward_noalloc on that device.
+tpcf_status noalloc_prepare(int dev) {
+    unsigned char* p = nullptr;
+    return scratch_address(dev, &p);
 }
 
 }  // namespace tpcf

@@ -13,6 +13,10 @@ namespace tpcf {
 tpcf_status cuda_fail(cudaError_t e, const char* where);
 // Records a message for tpcf_last_error().
 void set_error(const char* msg);
+// Every device allocation of the library goes through these two (api.cu): they keep
+// the count of live allocations and honour tpcf_test_fail_allocation().
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
 }  // namespace tpcf
 
 #define TRY_CUDA(call)                                                   \
@@ -57,13 +61,13 @@ struct tpcf_plan_s {
     template <typename T>
     cudaError_t alloc(T** p, size_t count) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        cudaError_t e = tpcf::dev_malloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
         if (e != cudaSuccess) return e;
         allocs.push_back(q);
         *p = (T*)q;
         return cudaSuccess;
     }
     ~tpcf_plan_s() {
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs) tpcf::dev_free(p);
     }
 };
