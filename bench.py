@@ -21,8 +21,11 @@ One step = one pass of the estimator over one batch of synthetic input:
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl gb300|reference]
 
-Under torchrun each rank runs an independent input of the same size on its own GPU
-(weak scaling, no data-path collective); rank 0 prints ONE JSON line.
+Under torchrun the map workloads split ONE map across the ranks (strong scaling:
+balanced pivot ranges, one FP64 all-reduce of (S, D) per forward, the adjoint by
+halo with the gradient sliced per rank); the catalogue and batch workloads run an
+independent input of the same size per GPU (weak scaling).  Rank 0 prints ONE JSON
+line.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -62,8 +65,9 @@ def map_workload(name):
     return getattr(synth, name)()
 
 
-def map_inputs(wl, rank: int):
-    """float32 (delta, w) of the workload; every rank gets an independent white-noise draw."""
+def map_inputs(wl, rank: int, same: bool = False):
+    """float32 (delta, w) of the workload; unless ``same``, every rank > 0 gets an
+    independent white-noise draw added."""
     import synth
     cache = "/dev/shm/tpcf_bench_%s_%d.npy" % (wl.name, wl.seed)
     if os.path.exists(cache):
@@ -76,7 +80,7 @@ def map_inputs(wl, rank: int):
                 os.replace(cache + ".tmp.npy", cache)
             except OSError:
                 pass
-    if rank > 0:
+    if rank > 0 and not same:
         d = d + (0.05 * synth.rng(wl.seed + 9000 + rank).standard_normal(d.shape[0])).astype(np.float32)
     return np.ascontiguousarray(d, np.float32), wl.weights().astype(np.float32)
 
@@ -273,6 +277,17 @@ def oracle_sample_catalog(xu, du, wu, edges, M, n_piv: int):
 
 # ---------------------------------------------------------------- GPU arm
 
+def autotune(args, plan, d_dev, w_dev):
+    """The plan's launch configuration, picked by the library's autotuner on this GPU
+    (set-up, outside the timed region; cached in TPCF_AUTOTUNE_CACHE when set)."""
+    if not args.autotune:
+        return dict(plan.launch_config(), autotuned=False)
+    t0 = time.time()
+    cfg = plan.autotune(d_dev, w_dev)
+    log("autotune: %s in %.1fs" % (cfg, time.time() - t0))
+    return dict(cfg, autotuned=True, seconds=round(time.time() - t0, 2))
+
+
 def setup_map(args, dev, rank):
     import torch
     from paper_2408_16847_gb300 import tpcf
@@ -281,14 +296,14 @@ def setup_map(args, dev, rank):
     t0 = time.time()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
-        # rank 0 paints the map once (cached in /dev/shm); the other ranks read the
-        # cache and add their own noise draw instead of painting concurrently
+        # one map split across the ranks: rank 0 paints it once (cached in /dev/shm),
+        # the other ranks read the cache
         import torch.distributed as dist
         if rank == 0:
-            d32, w32 = map_inputs(wl, rank)
+            d32, w32 = map_inputs(wl, rank, same=True)
         dist.barrier()
         if rank != 0:
-            d32, w32 = map_inputs(wl, rank)
+            d32, w32 = map_inputs(wl, rank, same=True)
     else:
         d32, w32 = map_inputs(wl, rank)
     log("[rank %d] inputs ready in %.1fs" % (rank, time.time() - t0))
@@ -307,7 +322,11 @@ def setup_map(args, dev, rank):
         first = 2 * n * (n - 1) + 4 * n * ((5 * n) // 4 - n)
         piv = (first, first + 4 * n * args.profile_band)
     total, n_sym, n_single = plan.count_pairs(w_dev, piv)
+    tune = autotune(args, plan, d_dev, w_dev)
     state = {}
+    if world > 1:
+        return setup_map_sharded(args, dev, rank, world, wl, plan, d32, w32, d_dev, w_dev, g_dev, total,
+                                 n_sym, n_single, tune)
     # the masked map's configuration is the forward + backward pass; the full-sky maps
     # time the forward and report the forward + adjoint beside it
     headline_both = args.pass_ == "both" or (args.pass_ == "auto" and wl.name == "masked_map_nside1024")
@@ -400,7 +419,7 @@ def setup_map(args, dev, rank):
                   args.profile_band, piv[1] - piv[0]),
               "l2": "inputs larger than L2 (%.2f GB of (w d, w) per map)" % (8 * 12 * wl.nside ** 2 / 1e9)
               if 12 * wl.nside ** 2 * 8 > 129e6 else "L2 flushed between steps",
-              "parallelism": "independent map per GPU"}
+              "parallelism": "independent map per GPU", "launch_config": tune}
     W = dict(step=step_fb if headline_both else step_fwd,
              split=("forward", "adjoint") if headline_both else ("forward", None),
              pairs=total, e2e=e2e_step, e2e_bytes=(in_bytes, out_bytes),
@@ -415,6 +434,77 @@ def setup_map(args, dev, rank):
             W["part_fb"] = dict(name="forward_adjoint", step=step_fb, warm=warm_adjoint, steps=args.fb_steps,
                                 roofline=lambda t1, t2, clk, sms: roof_fb(t1 + t2, t1, clk, sms))
     return W
+
+
+def setup_map_sharded(args, dev, rank, world, wl, plan, d32, w32, d_dev, w_dev, g_dev, total, n_sym, n_single,
+                      tune=None):
+    """One map's estimate split across the ranks (strong scaling): each rank runs the
+    forward over its balanced pivot range and one FP64 all-reduce of (S, D) gives
+    every rank zeta (shard.sharded_forward); the adjoint gives each rank its slice of
+    dL/d(delta) from the slice's halo pivots, with no reduction over the pixels
+    (shard.sharded_backward, gather=False)."""
+    import torch
+    from paper_2408_16847_gb300 import shard
+
+    K, M = wl.bins.nbins, wl.bins.m_max
+    state = {}
+
+    def step_fwd(ev=None):
+        state["zeta"], state["norm"] = shard.sharded_forward(plan, d_dev, w_dev)
+        if ev is not None:
+            ev.record(torch.cuda.current_stream())
+
+    def step_fb(ev=None):
+        zeta, norm = shard.sharded_forward(plan, d_dev, w_dev)
+        if ev is not None:
+            ev.record(torch.cuda.current_stream())
+        state["grad"] = shard.sharded_backward(plan, d_dev, w_dev, norm, g_dev, gather=False)
+
+    def warm_adjoint():
+        step_fb()
+
+    h_d = torch.from_numpy(d32).pin_memory()
+    h_w = torch.from_numpy(w32).pin_memory()
+    h_z = torch.empty((M + 1, K, K, 2), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        d = h_d.to(dev, non_blocking=True)
+        w = h_w.to(dev, non_blocking=True)
+        zeta, _ = shard.sharded_forward(plan, d, w)
+        h_z.copy_(zeta, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    f_single, f_mirror = flops_per_pair(M, adjoint=False)
+    fwd_alg = total * alg_flops_per_pair(M, False)
+
+    def roof_fwd(ms, clk, sms):
+        # whole-job flops over the slowest rank's time, against one GPU's peak x ranks
+        return {"bound": "alu", "kernel": "map_fwd_kernel", "achieved": fwd_alg / (ms * 1e-3) / 1e12,
+                "peak": fp32_peak_tflops(clk, sms) * world, "unit": "TFLOP/s",
+                "flops_per_pair": alg_flops_per_pair(M, False), "peak_note": "per-GPU peak x %d GPUs" % world,
+                "traffic": None}
+
+    def roof_fb(ms_total, ms_fwd, clk, sms):
+        ms_adj = ms_total - ms_fwd
+        return {"bound": "alu", "kernel": "map_bwd_kernel",
+                "achieved": total * alg_flops_per_pair(M, True) / (ms_adj * 1e-3) / 1e12,
+                "peak": fp32_peak_tflops(clk, sms) * world, "unit": "TFLOP/s",
+                "flops_per_pair": alg_flops_per_pair(M, True), "traffic": None}
+
+    config = {"workload": wl.name, "nside": wl.nside, "npix": 12 * wl.nside * wl.nside,
+              "bins": "%d log bins %.2f-%.2f deg" % (K, wl.bins.edges_deg[0], wl.bins.edges_deg[-1]),
+              "m_max": M, "pass": "forward", "pairs_per_step": total, "contraction": "FP32 pipe",
+              "pivots": "all", "l2": "inputs larger than L2",
+              "parallelism": "pivot ranges over %d GPUs, FP64 all-reduce of (S, D); adjoint by halo, "
+                             "gradient sliced per GPU" % world, "launch_config": tune}
+    return dict(step=step_fwd, split=("forward", None), pairs=total, scaling="strong", e2e=e2e_step,
+                e2e_bytes=(h_d.numel() * 4 + h_w.numel() * 4, h_z.numel() * 8),
+                vs_baseline=None, launches=plan.kernel_launches, config=config, cpu_baseline=None,
+                small_l2=False, close=plan.close,
+                roofline=lambda t1, t2, clk, sms: roof_fwd(t1, clk, sms),
+                part_fb=dict(name="forward_adjoint", step=step_fb, warm=warm_adjoint, steps=args.fb_steps,
+                             roofline=lambda t1, t2, clk, sms: roof_fb(t1 + t2, t1, clk, sms))
+                if args.fb_steps > 0 else None)
 
 
 def setup_catalog(args, dev, rank):
@@ -510,6 +600,8 @@ def setup_batch(args, dev, rank):
         plans.append(p)
         ds.append(torch.from_numpy(d32).to(dev))
         ws.append(torch.from_numpy(w32).to(dev))
+        if args.autotune:
+            p.autotune(ds[-1], ws[-1])  # the batch takes each member's tuned flush length
         zs.append(torch.empty((M + 1, K, K, 2), dtype=torch.float64, device=dev))
         ns.append(torch.empty((K, K), dtype=torch.float64, device=dev))
         g = torch.zeros((M + 1, K, K, 2), dtype=torch.float64, device=dev)
@@ -635,12 +727,15 @@ def run_gpu(args):
     t_setup = time.time()
     for _ in range(args.warmup):
         W["step"]()
+    torch.cuda.synchronize()
     log("[rank %d] %d warm-up steps in %.1fs" % (rank, args.warmup, time.time() - t_setup))
     launches0 = W["launches"]()
     total_ms, ms1, ms2, clk = timed(W["step"], args.steps)
     launches = W["launches"]() - launches0 + W.get("extra_launches_per_step", 0) * args.steps
     ms_step = total_ms / args.steps
-    value = world * W["pairs"] * args.steps / (total_ms * 1e-3)
+    strong = W.get("scaling") == "strong"
+    units = W["pairs"] if strong else world * W["pairs"]  # pairs of the whole job per step
+    value = units * args.steps / (total_ms * 1e-3)
     log("[rank %d] %d timed steps: %.1f ms/step" % (rank, args.steps, ms_step))
 
     e2e = None
@@ -661,7 +756,7 @@ def run_gpu(args):
         if world > 1:
             dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
         e2e_ms = float(e2e_ms.max().cpu())
-        e2e = {"value": world * W["pairs"] * args.e2e_steps / (e2e_ms * 1e-3), "unit": "pairs/s",
+        e2e = {"value": units * args.e2e_steps / (e2e_ms * 1e-3), "unit": "pairs/s",
                "h2d_bytes_per_step": W["e2e_bytes"][0], "d2h_bytes_per_step": W["e2e_bytes"][1],
                "steps": args.e2e_steps, "call": "tpcf_run_host (pinned host buffers)"}
 
@@ -674,7 +769,7 @@ def run_gpu(args):
         roof_p["frac"] = roof_p["achieved"] / roof_p["peak"]
         part = {"steps": P["steps"], "ms": p_tot / P["steps"], "forward_ms": p1 / P["steps"],
                 "adjoint_ms": p2 / P["steps"],
-                "value": world * W["pairs"] * P["steps"] / (p_tot * 1e-3), "unit": "pairs/s",
+                "value": units * P["steps"] / (p_tot * 1e-3), "unit": "pairs/s",
                 "roofline": roof_p, "clocks": p_clk}
         log("[rank %d] forward + adjoint: %.1f ms/step" % (rank, p_tot / P["steps"]))
 
@@ -708,7 +803,7 @@ def run_gpu(args):
             "warmup": args.warmup,
             "ms_per_step": ms_step,
             "higher_is_better": True,
-            "scaling": "weak",
+            "scaling": W.get("scaling", "weak"),
             "vs_baseline": (value / W["vs_baseline"]) if W.get("vs_baseline") else None,
             "dtype": "f32",
             "data": "synthetic",
@@ -790,6 +885,8 @@ def main():
     ap.add_argument("--contract", default="fp32", choices=["fp32", "tc"],
                     help="contraction of the map forward: FP32 pipe or tensor cores (TF32x3)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch configuration instead of running the autotuner")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -187,6 +187,41 @@ tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_t pivot_beg
                              int64_t* d_counts, void* stream);
 
 /*
+ * Autotuner of the map pair kernels' launch configuration (the paper has no GPU
+ * design; this picks the tile-processing shape on the device at hand).  Times the
+ * forward (passes bit 0) and/or the adjoint (bit 1) of the plan on a sample of pivots
+ * of the caller's field for every candidate -- register variant sized for 3 or 2
+ * resident CTAs per SM, CTAs per SM launched, rings summed in registers between
+ * shared-memory flushes -- and keeps the fastest in the plan.  With both passes and
+ * the environment variable TPCF_AUTOTUNE_CACHE naming a file, the result is appended
+ * there, keyed by device, nside, bins and flags; a later autotune call or
+ * tpcf_plan_create_map with the same key takes it from the file without measuring.
+ * Results do not depend on the configuration beyond summation order.  Allocates and
+ * frees temporaries (a gradient buffer of npoints floats for the adjoint);
+ * synchronises `stream`.  Map plans without TPCF_CONTRACT_TC only (else
+ * TPCF_ERR_UNSUPPORTED).
+ */
+tpcf_status tpcf_plan_autotune(tpcf_plan plan, const float* d_delta, const float* d_w, int32_t passes,
+                               void* stream);
+/* The plan's launch configuration: host int32[6] = forward (variant, CTAs per SM,
+ * flush rings), adjoint (variant, CTAs per SM, flush rings). */
+tpcf_status tpcf_plan_launch_config(tpcf_plan plan, int32_t* config6);
+/* Sets it (same layout); TPCF_ERR_INVALID_ARG for a configuration that does not fit. */
+tpcf_status tpcf_plan_set_launch_config(tpcf_plan plan, const int32_t* config6);
+
+/*
+ * Halo of a pixel range, for splitting the adjoint across devices (map plans): the
+ * smallest pixel range [*halo_begin, *halo_end) (whole HEALPix rings, RING order)
+ * that holds every pivot with a neighbour in [begin, end) (a neighbour lies within
+ * the outer bin edge, Sec. 3.1).  The adjoint restricted to the halo pivots is then
+ * exact on [begin, end), so a device that owns that slice of dL/d(delta) needs no
+ * contribution from the others.  An empty range gives an empty halo.  Host
+ * outputs; reads two entries of the plan's ring table (synchronous).  Catalogue
+ * plans: TPCF_ERR_UNSUPPORTED (their caller order has no spatial slices).
+ */
+tpcf_status tpcf_plan_halo(tpcf_plan plan, int64_t begin, int64_t end, int64_t* halo_begin, int64_t* halo_end);
+
+/*
  * End-to-end call on HOST buffers: copies h_delta and h_w to the device, runs the
  * forward over all pivots and, if h_dL_dzeta != NULL, the adjoint, and copies
  * zeta, norm and (if h_grad != NULL) the gradient back.  Uses device staging

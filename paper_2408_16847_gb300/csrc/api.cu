@@ -17,21 +17,21 @@ using namespace tpcf;
 
 namespace tpcf {
 // per-M launchers (map_inst.cu)
-#define TPCF_DECL_M(m)                                                                      \
-    cudaError_t map_fwd_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
-    cudaError_t map_fwd_tc_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);   \
-    int map_fwd_tc_occupancy_m##m(int, int);                                               \
-    cudaError_t map_bwd_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
-    int map_fwd_occupancy_m##m(int, int);                                                  \
-    int map_bwd_occupancy_m##m(int);                                                       \
-    size_t map_fwd_smem_m##m(int);                                                         \
+#define TPCF_DECL_M(m)                                                                         \
+    cudaError_t map_fwd_launch_m##m(const MapDev&, const MapCall&, int, int, cudaStream_t);    \
+    cudaError_t map_fwd_tc_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
+    int map_fwd_tc_occupancy_m##m(int, int);                                                  \
+    cudaError_t map_bwd_launch_m##m(const MapDev&, const MapCall&, int, int, cudaStream_t);    \
+    int map_fwd_occupancy_m##m(int, int, int);                                                \
+    int map_bwd_occupancy_m##m(int, int);                                                     \
+    size_t map_fwd_smem_m##m(int);                                                            \
     size_t map_bwd_smem_m##m(int);
 TPCF_DECL_M(0) TPCF_DECL_M(1) TPCF_DECL_M(2) TPCF_DECL_M(3) TPCF_DECL_M(4) TPCF_DECL_M(5)
 TPCF_DECL_M(6) TPCF_DECL_M(7) TPCF_DECL_M(8) TPCF_DECL_M(9) TPCF_DECL_M(10) TPCF_DECL_M(11)
 TPCF_DECL_M(12) TPCF_DECL_M(13) TPCF_DECL_M(14) TPCF_DECL_M(15) TPCF_DECL_M(16)
 #undef TPCF_DECL_M
-cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi,
-                             unsigned long long* counts, int grid, cudaStream_t s);
+cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi, long long tlo,
+                             long long thi, unsigned long long* counts, int grid, cudaStream_t s);
 // catalogue plans (catalog.cu)
 tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaStream_t s);
 tpcf_status catalog_count(tpcf_plan_s* P, const float* d_w, int64_t lo, int64_t hi, int64_t* d_counts,
@@ -44,12 +44,12 @@ tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d
 tpcf_status noalloc_prepare(int dev);
 
 struct MLaunch {
-    cudaError_t (*fwd)(const MapDev&, const MapCall&, int, cudaStream_t);
+    cudaError_t (*fwd)(const MapDev&, const MapCall&, int, int, cudaStream_t);
     cudaError_t (*fwd_tc)(const MapDev&, const MapCall&, int, cudaStream_t);
     int (*fwd_tc_occ)(int, int);
-    cudaError_t (*bwd)(const MapDev&, const MapCall&, int, cudaStream_t);
-    int (*fwd_occ)(int, int);
-    int (*bwd_occ)(int);
+    cudaError_t (*bwd)(const MapDev&, const MapCall&, int, int, cudaStream_t);
+    int (*fwd_occ)(int, int, int);
+    int (*bwd_occ)(int, int);
     size_t (*fwd_smem)(int);
     size_t (*bwd_smem)(int);
 };
@@ -60,6 +60,12 @@ static const MLaunch kLaunch[TPCF_MAX_M + 1] = {
     TPCF_ROW_M(6),  TPCF_ROW_M(7),  TPCF_ROW_M(8),  TPCF_ROW_M(9),  TPCF_ROW_M(10), TPCF_ROW_M(11),
     TPCF_ROW_M(12), TPCF_ROW_M(13), TPCF_ROW_M(14), TPCF_ROW_M(15), TPCF_ROW_M(16)};
 #undef TPCF_ROW_M
+
+// resident CTAs per SM of each register variant (used by the autotuner, tune.cu)
+int map_fwd_occupancy(int M, int K, int self, int variant) { return kLaunch[M].fwd_occ(K, self, variant); }
+int map_bwd_occupancy(int M, int K, int variant) { return kLaunch[M].bwd_occ(K, variant); }
+// applies a configuration cached by the autotuner (tune.cu)
+void tune_from_cache(tpcf_plan_s* P);
 }  // namespace tpcf
 
 static thread_local char g_last_error[256] = "";
@@ -183,6 +189,8 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     TRY_CUDA(cudaMemcpyAsync(totals, tot, sizeof(totals), cudaMemcpyDeviceToHost, s));
     TRY_CUDA(cudaStreamSynchronize(s));
     const int64_t npairs = totals[0], ntiles = totals[1];
+    P->tile_off_h.resize(nrings);
+    TRY_CUDA(cudaMemcpy(P->tile_off_h.data(), tile_off, sizeof(int64_t) * nrings, cudaMemcpyDeviceToHost));
     float2* pair_A;
     int2 *pair_T, *tiles;
     TRY_CUDA(P->alloc(&pair_A, npairs));
@@ -216,14 +224,19 @@ static tpcf_status build_map(tpcf_plan_s* P, int64_t nside, cudaStream_t s) {
     const MLaunch& L = kLaunch[P->M];
     const int self = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
     const bool tc = (P->flags & TPCF_CONTRACT_TC) != 0;
-    int occ_f = tc ? L.fwd_tc_occ(K, self) : L.fwd_occ(K, self);
-    int occ_b = L.bwd_occ(K);
+    int occ_f = tc ? L.fwd_tc_occ(K, self) : std::max(L.fwd_occ(K, self, 3), L.fwd_occ(K, self, 2));
+    int occ_b = std::max(L.bwd_occ(K, 3), L.bwd_occ(K, 2));
     if (occ_f < 1 || occ_b < 1) {
         snprintf(g_last_error, sizeof(g_last_error), "kernel does not fit (K=%d, M=%d)", K, P->M);
         return TPCF_ERR_UNSUPPORTED;
     }
+    // slots for the largest grid any configuration launches
     P->fwd_grid = (int)std::min<int64_t>(ntiles, (int64_t)P->num_sms * occ_f);
     P->bwd_grid = (int)std::min<int64_t>(ntiles, (int64_t)P->num_sms * occ_b);
+    P->tune_fwd.ctas = tc ? occ_f : L.fwd_occ(K, self, 3);
+    P->tune_bwd.ctas = L.bwd_occ(K, 3);
+    if (P->tune_fwd.ctas < 1) P->tune_fwd.variant = 2, P->tune_fwd.ctas = L.fwd_occ(K, self, 2);
+    if (P->tune_bwd.ctas < 1) P->tune_bwd.variant = 2, P->tune_bwd.ctas = L.bwd_occ(K, 2);
     if (P->fwd_grid < 1) P->fwd_grid = 1;
     if (P->bwd_grid < 1) P->bwd_grid = 1;
     P->nent = n_entries(K, P->M);
@@ -265,6 +278,7 @@ extern "C" tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const
         delete P;
         return st;
     }
+    tune_from_cache(P);
     // place tpcf_forward_noalloc's fixed scratch on this device now, during set-up;
     // on failure that call reports it, so clear the runtime's last-error state here
     if (noalloc_prepare(P->device) != TPCF_OK) cudaGetLastError();
@@ -314,6 +328,46 @@ extern "C" int64_t tpcf_plan_npoints(tpcf_plan plan) { return plan ? plan->npoin
 
 extern "C" int64_t tpcf_plan_kernel_launches(tpcf_plan plan) { return plan ? plan->launches : -1; }
 
+// 0-based ring of RING-order pixel p (HEALPix, Gorski et al. 2005).
+static int64_t ring_of_pixel(int64_t nside, int64_t p) {
+    const int64_t ncap = 2 * nside * (nside - 1), npix = 12 * nside * nside;
+    auto cap_ring = [](int64_t q) {  // 1-based ring r of the north cap holding q: 2r(r-1) <= q
+        int64_t r = (int64_t)((1.0 + sqrt(1.0 + 2.0 * (double)q)) * 0.5);
+        while (2 * r * (r - 1) > q) --r;
+        while (2 * (r + 1) * r <= q) ++r;
+        return r;
+    };
+    if (p < ncap) return cap_ring(p) - 1;
+    if (p < npix - ncap) return (p - ncap) / (4 * nside) + nside - 1;
+    return 4 * nside - 1 - cap_ring(npix - 1 - p);
+}
+
+static int64_t ring_first_pixel(int64_t nside, int64_t ri) {  // 0-based ring
+    const int64_t r = ri + 1;
+    if (r < nside) return 2 * r * (r - 1);
+    if (r <= 3 * nside) return 2 * nside * (nside - 1) + 4 * nside * (r - nside);
+    const int64_t rr = 4 * nside - r;
+    return 12 * nside * nside - 2 * rr * (rr + 1);
+}
+
+// Tiles [*tlo, *thi) that hold the pivots [lo, hi) (tiles are 32 consecutive pixels
+// of one ring, rings in order).
+static void tile_range(const tpcf_plan_s* P, int64_t lo, int64_t hi, int64_t* tlo, int64_t* thi) {
+    if (hi <= lo) {
+        *tlo = *thi = 0;
+        return;
+    }
+    const int64_t nside = P->map.nside;
+    const int64_t ra = ring_of_pixel(nside, lo), rb = ring_of_pixel(nside, hi - 1);
+    *tlo = P->tile_off_h[ra] + (lo - ring_first_pixel(nside, ra)) / TILE;
+    *thi = P->tile_off_h[rb] + (hi - 1 - ring_first_pixel(nside, rb)) / TILE + 1;
+}
+
+static int launch_grid(const tpcf_plan_s* P, const tpcf_plan_s::Tune& t, int64_t ntiles, int cap) {
+    const int64_t g = std::min<int64_t>(ntiles, (int64_t)P->num_sms * t.ctas);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
 static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
                                double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s) {
     const MapDev& g = P->map;
@@ -329,10 +383,13 @@ static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float
     c.counter = P->counter;
     c.status = P->status;
     c.self_subtract = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
+    c.flush = P->tune_fwd.flush;
+    tile_range(P, lo, hi, &c.tile_lo, &c.tile_hi);
+    const int grid = launch_grid(P, P->tune_fwd, c.tile_hi - c.tile_lo, P->fwd_grid);
     if (P->flags & TPCF_CONTRACT_TC)
-        TRY_CUDA(kLaunch[P->M].fwd_tc(g, c, P->fwd_grid, s));
+        TRY_CUDA(kLaunch[P->M].fwd_tc(g, c, grid, s));
     else
-        TRY_CUDA(kLaunch[P->M].fwd(g, c, P->fwd_grid, s));
+        TRY_CUDA(kLaunch[P->M].fwd(g, c, grid, P->tune_fwd.variant, s));
     reduce_slots_kernel<<<n_blocks(P->nent, 128), 128, 0, s>>>(P->slots, P->fwd_grid, P->nent, P->sums);
     const int nout = (P->M + 1) * P->K * P->K;
     finalize_kernel<<<n_blocks(nout, 128), 128, 0, s>>>(P->sums, P->K, P->M, c.self_subtract, 1.0, d_zeta,
@@ -368,7 +425,9 @@ extern "C" tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_
     pack_kernel<<<plan->num_sms * 8, 256, 0, s>>>(d_w, d_w, plan->wdw, g.npix);
     plan->launches += 2;
     TRY_CUDA(cudaMemsetAsync(d_counts, 0, 3 * sizeof(int64_t), s));
-    TRY_CUDA(map_count_launch(g, plan->wdw, pivot_begin, pivot_end, (unsigned long long*)d_counts,
+    int64_t tlo, thi;
+    tile_range(plan, pivot_begin, pivot_end, &tlo, &thi);
+    TRY_CUDA(map_count_launch(g, plan->wdw, pivot_begin, pivot_end, tlo, thi, (unsigned long long*)d_counts,
                               plan->num_sms * 4, s));
     return TPCF_OK;
 }
@@ -392,7 +451,10 @@ static tpcf_status map_backward(tpcf_plan_s* P, const float* d_delta, const floa
     c.H = P->H;
     c.grad = d_grad;
     c.self_subtract = self;
-    TRY_CUDA(kLaunch[P->M].bwd(g, c, P->bwd_grid, s));
+    c.flush = P->tune_bwd.flush;
+    tile_range(P, lo, hi, &c.tile_lo, &c.tile_hi);
+    const int grid = launch_grid(P, P->tune_bwd, c.tile_hi - c.tile_lo, P->bwd_grid);
+    TRY_CUDA(kLaunch[P->M].bwd(g, c, grid, P->tune_bwd.variant, s));
     return TPCF_OK;
 }
 
@@ -408,6 +470,30 @@ extern "C" tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const
     if (plan->kind == PLAN_CATALOG)
         return catalog_backward(plan, d_delta, d_w, pivot_begin, pivot_end, d_norm, d_dL_dzeta, d_grad, s);
     return TPCF_ERR_UNSUPPORTED;
+}
+
+extern "C" tpcf_status tpcf_plan_halo(tpcf_plan plan, int64_t begin, int64_t end, int64_t* halo_begin,
+                                      int64_t* halo_end) {
+    if (!plan || !halo_begin || !halo_end) return TPCF_ERR_INVALID_ARG;
+    if (begin < 0 || end < begin || end > plan->npoints) return TPCF_ERR_INVALID_ARG;
+    if (plan->kind != PLAN_MAP) {
+        set_error("tpcf_plan_halo: map plans only");
+        return TPCF_ERR_UNSUPPORTED;
+    }
+    if (begin == end) {
+        *halo_begin = *halo_end = begin;
+        return TPCF_OK;
+    }
+    const int64_t nside = plan->map.nside;
+    const int64_t ra = ring_of_pixel(nside, begin), rb = ring_of_pixel(nside, end - 1);
+    int2 wa, wb;
+    // ring windows are symmetric (ring r is in reach of ring i iff i is in reach of r)
+    // and monotone in the ring index, so the halo rings are those of the end rings
+    TRY_CUDA(cudaMemcpy(&wa, plan->map.ring_range + ra, sizeof(int2), cudaMemcpyDeviceToHost));
+    TRY_CUDA(cudaMemcpy(&wb, plan->map.ring_range + rb, sizeof(int2), cudaMemcpyDeviceToHost));
+    *halo_begin = ring_first_pixel(nside, wa.x);
+    *halo_end = ring_first_pixel(nside, (int64_t)wb.y + 1);
+    return TPCF_OK;
 }
 
 extern "C" tpcf_status tpcf_run_host(tpcf_plan plan, const float* h_delta, const float* h_w,

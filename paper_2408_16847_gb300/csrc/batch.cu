@@ -225,6 +225,9 @@ static tpcf_status batch_build(tpcf_batch_s* B, const tpcf_plan* plans, const fl
             it.c.H = P->H;
             it.c.grad = io[i].grad;
             it.c.self_subtract = io[i].self_subtract;
+            it.c.flush = P->tune_fwd.flush;
+            it.c.tile_lo = 0;
+            it.c.tile_hi = P->map.ntiles;
             it.tile0 = t0;
             t0 += P->map.ntiles;
             items.push_back(it);

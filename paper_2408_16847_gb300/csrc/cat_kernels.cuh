@@ -238,6 +238,142 @@ __device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restri
     }
 }
 
+// The candidates of the cap grouped by bin, chunk by chunk.  For each staged chunk of
+// 32 candidates, pass A bins every candidate for the lane's pivot and records, per
+// lane, one bit mask per bin kb + j (j = 0..GROUPS-1, kb = the first in-range bin seen
+// in the chunk minus one; a tile's pivots lie close together, so the candidates of a
+// chunk cover few bins for every lane) plus a mask of the rare in-range candidates
+// beyond that window; out-of-range candidates are dropped there.  Pass B then runs,
+// for each j in lockstep, every lane over the candidates of its own bin kb + j:
+//     pair(active, k, dx, dy, dz, v, u)   for each candidate (u its slot in the chunk;
+//                                         active false on padding iterations, where k
+//                                         may be out of range and must not be used)
+//     group_end(k, nonempty)              once per j, warp-uniform
+// and the candidates beyond the window one by one: single(k, dx, dy, dz, v, u).
+// chunk_end(base, cnt) closes each chunk (uniform).  This replaces per-candidate bin
+// changes (a divergent flush whenever one lane's bin changed) by a uniform flush per
+// bin and chunk.
+constexpr int CAT_GROUPS = 4;
+
+template <class FP, class FE, class FS, class FC>
+__device__ __forceinline__ void cat_walk_grouped(const CatDev& g, const float2* __restrict__ wdw,
+                                                 const double* s_cap, const CatPivot& P, const float* sE2,
+                                                 const unsigned char* slut, float4* wh, float4* wl, float2* wv,
+                                                 FP&& pair, FE&& group_end, FS&& single, FC&& chunk_end) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = g.K;
+    const float phc = (float)s_cap[0], dphi = (float)s_cap[1] + 4.0e-6f;
+    const int b0 = (int)s_cap[2], b1 = (int)s_cap[3];
+    const bool full = s_cap[4] != 0.0;
+    int chunk = 0;
+    for (int b = b0; b <= b1; ++b) {
+        const int64_t ns = g.band_ns[b];
+        const int64_t cf = g.band_first[b];
+        int64_t ca0 = cf, ca1 = cf + ns, cb0 = 0, cb1 = 0;
+        if (!full) {
+            const float scale = (float)ns * (float)(0.5 / M_PI);
+            const int64_t sa = (int64_t)floorf((phc - dphi) * scale);
+            const int64_t sb = (int64_t)floorf((phc + dphi) * scale);
+            const int64_t len = sb - sa + 1;
+            if (len < ns) {
+                int64_t s0 = sa % ns;
+                if (s0 < 0) s0 += ns;
+                ca0 = cf + s0;
+                if (s0 + len <= ns) {
+                    ca1 = cf + s0 + len;
+                } else {
+                    ca1 = cf + ns;
+                    cb0 = cf;
+                    cb1 = cf + (s0 + len - ns);
+                }
+            }
+        }
+#pragma unroll 1
+        for (int sg = 0; sg < 2; ++sg) {
+            const int64_t cl0 = sg == 0 ? ca0 : cb0, cl1 = sg == 0 ? ca1 : cb1;
+            if (cl1 <= cl0) continue;
+            const int64_t p0 = g.cell_start[cl0], p1 = g.cell_start[cl1];
+            for (int64_t base = p0; base < p1; base += TILE, ++chunk) {
+                if ((chunk % NWARPS) != warp) continue;
+                const int64_t j = base + lane;
+                __syncwarp();
+                if (j < p1) {
+                    wh[lane] = g.p_hi[j];
+                    wl[lane] = g.p_lo[j];
+                    wv[lane] = wdw[j];
+                }
+                __syncwarp();
+                const int cnt = (int)min((int64_t)TILE, p1 - base);
+                // pass A: bins, per-lane masks
+                unsigned mk[CAT_GROUPS];
+#pragma unroll
+                for (int q = 0; q < CAT_GROUPS; ++q) mk[q] = 0u;
+                unsigned mo = 0u;
+                int kb = -1000;
+                for (int u = 0; u < cnt; ++u) {
+                    const float4 qh = wh[u], ql = wl[u];
+                    const float dx = (qh.x - P.hx) + (ql.x - P.lx);
+                    const float dy = (qh.y - P.hy) + (ql.y - P.ly);
+                    const float dz = (qh.z - P.hz) + (ql.z - P.lz);
+                    const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
+                    const int e1 = max(k, 0), e2 = min(k + 1, K);
+                    if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
+                        k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.px, P.py, P.pz);
+                    if (k < 0 || k >= K) continue;
+                    if (kb == -1000) kb = max(k - 1, 0);
+                    const int q = k - kb;
+                    const unsigned bit = 1u << u;
+#pragma unroll
+                    for (int r = 0; r < CAT_GROUPS; ++r)
+                        if (q == r) mk[r] |= bit;
+                    if (q < 0 || q >= CAT_GROUPS) mo |= bit;
+                }
+                // pass B: per bin of the window, in lockstep
+#pragma unroll 1
+                for (int r = 0; r < CAT_GROUPS; ++r) {
+                    unsigned msk = 0u;
+#pragma unroll
+                    for (int q = 0; q < CAT_GROUPS; ++q)
+                        if (q == r) msk = mk[q];
+                    const bool had = msk != 0u;
+                    if (!__any_sync(0xffffffffu, had)) continue;
+                    while (__any_sync(0xffffffffu, msk != 0u)) {
+                        const bool active = msk != 0u;
+                        const int u = active ? __ffs(msk) - 1 : 0;
+                        msk &= msk - 1u;
+                        const float4 qh = wh[u], ql = wl[u];
+                        const float dx = (qh.x - P.hx) + (ql.x - P.lx);
+                        const float dy = (qh.y - P.hy) + (ql.y - P.ly);
+                        const float dz = (qh.z - P.hz) + (ql.z - P.lz);
+                        pair(active, kb + r, dx, dy, dz, wv[u], u);
+                    }
+                    group_end(kb + r, had);
+                }
+                // the rare in-range candidates outside the window, one by one
+                while (__any_sync(0xffffffffu, mo != 0u)) {
+                    const bool active = mo != 0u;
+                    const int u = active ? __ffs(mo) - 1 : 0;
+                    mo &= mo - 1u;
+                    if (active) {
+                        const float4 qh = wh[u], ql = wl[u];
+                        const float dx = (qh.x - P.hx) + (ql.x - P.lx);
+                        const float dy = (qh.y - P.hy) + (ql.y - P.ly);
+                        const float dz = (qh.z - P.hz) + (ql.z - P.lz);
+                        const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
+                        const int e1 = max(k, 0), e2 = min(k + 1, K);
+                        if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
+                            k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.px, P.py, P.pz);
+                        single(k, dx, dy, dz, wv[u], u);
+                    }
+                }
+                chunk_end(base, cnt);
+            }
+        }
+    }
+}
+
 template <int M, bool SELF>
 __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall c) {
     extern __shared__ __align__(16) float smem[];
@@ -294,27 +430,40 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
 #pragma unroll
         for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
         float W = 0.0f, Qs = 0.0f, QW = 0.0f;
-        int kcur = -1;
-        cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
-                 [&](int k, float dx, float dy, float dz, float2 v, int) {
-                     const bool on = k >= 0 && k < K;
-                     if (on && k != kcur) {
-                         if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
-                         kcur = k;
-                     }
-                     const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
-                     const float E = fmaf(dx, P.ex, dy * P.ey);
-                     const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
-                     const float wd = on ? v.x : 0.0f;
-                     const float ww = on ? v.y : 0.0f;
-                     harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
-                     W += ww;
-                     if (SELF) {
-                         Qs = fmaf(wd, wd, Qs);
-                         QW = fmaf(ww, ww, QW);
-                     }
-                 });
-        if (kcur >= 0) cat_flush<M, SELF>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
+        cat_walk_grouped(
+            g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+            [&](bool active, int, float dx, float dy, float dz, float2 v, int) {
+                const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                const float E = fmaf(dx, P.ex, dy * P.ey);
+                const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                const float wd = active ? v.x : 0.0f;
+                const float ww = active ? v.y : 0.0f;
+                harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
+                W += ww;
+                if (SELF) {
+                    Qs = fmaf(wd, wd, Qs);
+                    QW = fmaf(ww, ww, QW);
+                }
+            },
+            [&](int k, bool had) {
+                if (had) {
+                    cat_flush<M, SELF>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
+                }
+            },
+            [&](int k, float dx, float dy, float dz, float2 v, int) {
+                // every group is flushed by now, so the register sums are free
+                const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                const float E = fmaf(dx, P.ex, dy * P.ey);
+                const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                harmonics<M>(acc, N * rinv, E * rinv, v.x, v.x);
+                W = v.y;
+                if (SELF) {
+                    Qs = v.x * v.x;
+                    QW = v.y * v.y;
+                }
+                cat_flush<M, SELF>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
+            },
+            [&](int64_t, int) {});
         __syncthreads();
         tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
         __syncthreads();
@@ -325,7 +474,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
 // primary-term sums.
 template <int M>
 __host__ __device__ inline size_t cat_bwd_bytes(int K) {
-    return cat_tile_bytes<M>(K) + ((size_t)K * K * 2 + TILE) * sizeof(float);
+    return cat_tile_bytes<M>(K) + ((size_t)K * K * 2 + TILE + NWARPS * TILE) * sizeof(float);
 }
 
 // Catalogue adjoint, dL/d(delta_p) (the map adjoint's three phases on the catalogue
@@ -351,7 +500,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall 
     float4* sCl = sCh + NWARPS * TILE;
     float2* sCv = reinterpret_cast<float2*>(sCl + NWARPS * TILE);
     float* sHm = reinterpret_cast<float*>(sCv + NWARPS * TILE);  // [K][K][2], one m at a time
-    float* sPrim = sHm + (size_t)K * K * 2;
+    float* sPrim = sHm + (size_t)K * K * 2;                       // [TILE], then sG [NWARPS][TILE]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t nfl = tile_floats<M>(K) - 2 * TILE;
     for (int e = threadIdx.x; e <= K; e += NTHREADS) sE2[e] = g.E2[e];
@@ -395,22 +544,28 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall 
 #pragma unroll
             for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
             float W = 0.0f, Qs = 0.0f, QW = 0.0f;
-            int kcur = -1;
-            cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
-                     [&](int k, float dx, float dy, float dz, float2 v, int) {
-                         const bool on = k >= 0 && k < K;
-                         if (on && k != kcur) {
-                             if (kcur >= 0) cat_flush<M, false>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
-                             kcur = k;
-                         }
-                         const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
-                         const float E = fmaf(dx, P.ex, dy * P.ey);
-                         const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
-                         const float wd = on ? v.x : 0.0f;
-                         harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
-                         W += on ? v.y : 0.0f;
-                     });
-            if (kcur >= 0) cat_flush<M, false>(sA, sW, sQ, sQW, kcur, lane, acc, W, Qs, QW);
+            cat_walk_grouped(
+                g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+                [&](bool active, int, float dx, float dy, float dz, float2 v, int) {
+                    const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                    const float E = fmaf(dx, P.ex, dy * P.ey);
+                    const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                    const float wd = active ? v.x : 0.0f;
+                    harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
+                    W += active ? v.y : 0.0f;
+                },
+                [&](int k, bool had) {
+                    if (had) cat_flush<M, false>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
+                },
+                [&](int k, float dx, float dy, float dz, float2 v, int) {
+                    const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                    const float E = fmaf(dx, P.ex, dy * P.ey);
+                    const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                    harmonics<M>(acc, N * rinv, E * rinv, v.x, v.x);
+                    W = v.y;
+                    cat_flush<M, false>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
+                },
+                [&](int64_t, int) {});
         }
         __syncthreads();
         // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
@@ -449,34 +604,57 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall 
             const float gp = 0.5f * pv.y * sPrim[lane];
             if (gp != 0.0f) atomicAdd(c.grad + oi, gp);
         }
-        // phase 3: the neighbour legs, summed over the warp's 32 pivots per candidate
+        // phase 3: the neighbour legs; each candidate's contributions from the warp's
+        // 32 pivots are summed in the warp's shared buffer sG, then added once to its
+        // gradient entry at the end of the chunk
         {
             float2 h[M + 1];
             int kh = -1;
             const float wdi = pv.x;
-            cat_walk(g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
-                     [&](int k, float dx, float dy, float dz, float2 v, int j) {
-                         const bool on = k >= 0 && k < K && wdi != 0.0f;
-                         float val = 0.0f;
-                         if (on) {
-                             if (k != kh) {
-                                 const float* hk = sA + (size_t)k * (M + 1) * 2 * TILE;
+            float* sG = sPrim + TILE + warp * TILE;
+            sG[lane] = 0.0f;
+            __syncwarp();
+            auto load_h = [&](int k) {
+                const float* hk = sA + (size_t)k * (M + 1) * 2 * TILE;
 #pragma unroll
-                                 for (int m = 0; m <= M; ++m)
-                                     h[m] = make_float2(hk[(2 * m) * TILE + lane], hk[(2 * m + 1) * TILE + lane]);
-                                 kh = k;
-                             }
-                             const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
-                             const float E = fmaf(dx, P.ex, dy * P.ey);
-                             const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
-                             float X, Y;
-                             adj_harmonics<M>(h, N * rinv, E * rinv, X, Y);
-                             val = wdi * v.y * (X + Y);
-                         }
-#pragma unroll
-                         for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-                         if (lane == 0 && val != 0.0f) atomicAdd(c.grad + g.orig[j], val);
-                     });
+                for (int m = 0; m <= M; ++m)
+                    h[m] = make_float2(hk[(2 * m) * TILE + lane], hk[(2 * m + 1) * TILE + lane]);
+                kh = k;
+            };
+            auto leg = [&](float dx, float dy, float dz, float2 v) {
+                const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+                const float E = fmaf(dx, P.ex, dy * P.ey);
+                const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+                float X, Y;
+                adj_harmonics<M>(h, N * rinv, E * rinv, X, Y);
+                return wdi * v.y * (X + Y);
+            };
+            cat_walk_grouped(
+                g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+                [&](bool active, int k, float dx, float dy, float dz, float2 v, int u) {
+                    // an inactive lane may have no valid bin in this chunk (k is then
+                    // out of range): it neither loads h nor adds anything
+                    if (active) {
+                        if (k != kh) load_h(k);
+                        const float val = leg(dx, dy, dz, v);
+                        if (val != 0.0f) atomicAdd(sG + u, val);
+                    }
+                },
+                [&](int, bool) {},
+                [&](int k, float dx, float dy, float dz, float2 v, int u) {
+                    load_h(k);
+                    const float val = leg(dx, dy, dz, v);
+                    if (val != 0.0f) atomicAdd(sG + u, val);
+                },
+                [&](int64_t base, int cnt) {
+                    __syncwarp();
+                    if (lane < cnt) {
+                        const float val = sG[lane];
+                        if (val != 0.0f) atomicAdd(c.grad + g.orig[base + lane], val);
+                        sG[lane] = 0.0f;
+                    }
+                    __syncwarp();
+                });
         }
         __syncthreads();
     }

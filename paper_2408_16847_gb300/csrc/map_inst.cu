@@ -11,76 +11,71 @@
 
 namespace tpcf {
 
-cudaError_t TPCF_CAT(map_fwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid,
+// Launch the pair kernel `k` with `smem` bytes of dynamic shared memory.
+template <class Kern>
+static cudaError_t launch(Kern* k, size_t smem, int grid, const MapDev& g, const MapCall& c, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(g, c);
+    return cudaGetLastError();
+}
+
+template <class Kern>
+static int occupancy(Kern* k, size_t smem) {
+    int nb = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NTHREADS, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+// The forward pair kernel; variant 3 or 2 = CTAs per SM its registers are sized for.
+cudaError_t TPCF_CAT(map_fwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid, int variant,
                                                cudaStream_t s) {
     const size_t smem = tile_floats<TPCF_M>(g.K) * sizeof(float);
-    if (c.self_subtract) {
-        auto* k = map_fwd_kernel<TPCF_M, true, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, NTHREADS, smem, s>>>(g, c);
-    } else {
-        auto* k = map_fwd_kernel<TPCF_M, false, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, NTHREADS, smem, s>>>(g, c);
-    }
-    return cudaGetLastError();
+    if (c.self_subtract)
+        return variant == 2 ? launch(map_fwd_kernel<TPCF_M, true, false, 2>, smem, grid, g, c, s)
+                            : launch(map_fwd_kernel<TPCF_M, true, false, 3>, smem, grid, g, c, s);
+    return variant == 2 ? launch(map_fwd_kernel<TPCF_M, false, false, 2>, smem, grid, g, c, s)
+                        : launch(map_fwd_kernel<TPCF_M, false, false, 3>, smem, grid, g, c, s);
 }
 
-cudaError_t TPCF_CAT(map_bwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid,
+cudaError_t TPCF_CAT(map_bwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid, int variant,
                                                cudaStream_t s) {
     const size_t smem = bwd_tile_floats<TPCF_M>(g.K) * sizeof(float);
-    if (c.self_subtract) {
-        auto* k = map_bwd_kernel<TPCF_M, true>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, NTHREADS, smem, s>>>(g, c);
-    } else {
-        auto* k = map_bwd_kernel<TPCF_M, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, NTHREADS, smem, s>>>(g, c);
-    }
-    return cudaGetLastError();
+    if (c.self_subtract)
+        return variant == 2 ? launch(map_bwd_kernel<TPCF_M, true, 2>, smem, grid, g, c, s)
+                            : launch(map_bwd_kernel<TPCF_M, true, 3>, smem, grid, g, c, s);
+    return variant == 2 ? launch(map_bwd_kernel<TPCF_M, false, 2>, smem, grid, g, c, s)
+                        : launch(map_bwd_kernel<TPCF_M, false, 3>, smem, grid, g, c, s);
 }
 
-int TPCF_CAT(map_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
+// Resident CTAs per SM of the forward variant (shared memory and registers).
+int TPCF_CAT(map_fwd_occupancy_m, TPCF_M)(int K, int self_subtract, int variant) {
     const size_t smem = tile_floats<TPCF_M>(K) * sizeof(float);
-    int nb = 0;
-    if (self_subtract) {
-        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, true, false>, NTHREADS, smem);
-    } else {
-        cudaFuncSetAttribute(map_fwd_kernel<TPCF_M, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_kernel<TPCF_M, false, false>, NTHREADS, smem);
-    }
-    return nb;
+    if (self_subtract)
+        return variant == 2 ? occupancy(map_fwd_kernel<TPCF_M, true, false, 2>, smem)
+                            : occupancy(map_fwd_kernel<TPCF_M, true, false, 3>, smem);
+    return variant == 2 ? occupancy(map_fwd_kernel<TPCF_M, false, false, 2>, smem)
+                        : occupancy(map_fwd_kernel<TPCF_M, false, false, 3>, smem);
 }
 
-int TPCF_CAT(map_bwd_occupancy_m, TPCF_M)(int K) {
+// Resident CTAs per SM of the adjoint variant (either self-pair mode).
+int TPCF_CAT(map_bwd_occupancy_m, TPCF_M)(int K, int variant) {
     const size_t smem = bwd_tile_floats<TPCF_M>(K) * sizeof(float);
-    int nb = 0;
-    cudaFuncSetAttribute(map_bwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_bwd_kernel<TPCF_M, false>, NTHREADS, smem);
-    int nb_self = 0;
-    cudaFuncSetAttribute(map_bwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_self, map_bwd_kernel<TPCF_M, true>, NTHREADS, smem);
-    if (nb_self < nb) nb = nb_self;
-    return nb;
+    int a, b;
+    if (variant == 2) {
+        a = occupancy(map_bwd_kernel<TPCF_M, false, 2>, smem);
+        b = occupancy(map_bwd_kernel<TPCF_M, true, 2>, smem);
+    } else {
+        a = occupancy(map_bwd_kernel<TPCF_M, false, 3>, smem);
+        b = occupancy(map_bwd_kernel<TPCF_M, true, 3>, smem);
+    }
+    return a < b ? a : b;
 }
 
 // Forward with the split-precision tensor-core contraction.
-static size_t fwd_tc_smem(int K) {
-    const size_t a = tc_region_bytes(K) + tile_floats<TPCF_M>(K) * sizeof(float);
-    const size_t b = tc_min_total_bytes(K);
-    return a > b ? a : b;
-}
-
 cudaError_t TPCF_CAT(map_fwd_tc_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid, cudaStream_t s) {
-    const size_t smem = fwd_tc_smem(g.K);
+    const size_t smem = tc_smem_bytes(g.K, TPCF_M, c.self_subtract != 0);
     if (c.self_subtract) {
         auto* k = map_fwd_tc_kernel<TPCF_M, true>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -96,7 +91,7 @@ cudaError_t TPCF_CAT(map_fwd_tc_launch_m, TPCF_M)(const MapDev& g, const MapCall
 }
 
 int TPCF_CAT(map_fwd_tc_occupancy_m, TPCF_M)(int K, int self_subtract) {
-    const size_t smem = fwd_tc_smem(K);
+    const size_t smem = tc_smem_bytes(K, TPCF_M, self_subtract != 0);
     int nb = 0;
     if (self_subtract) {
         cudaFuncSetAttribute(map_fwd_tc_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -228,9 +223,9 @@ cudaError_t cat_count_launch(const CatDev& g, const float2* wdw, long long lo, l
     return cudaGetLastError();
 }
 
-cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi,
-                             unsigned long long* counts, int grid, cudaStream_t s) {
-    map_count_kernel<<<grid, NTHREADS, 0, s>>>(g, wdw, lo, hi, counts);
+cudaError_t map_count_launch(const MapDev& g, const float2* wdw, long long lo, long long hi, long long tlo,
+                             long long thi, unsigned long long* counts, int grid, cudaStream_t s) {
+    map_count_kernel<<<grid, NTHREADS, 0, s>>>(g, wdw, lo, hi, tlo, thi, counts);
     return cudaGetLastError();
 }
 #endif

@@ -34,7 +34,7 @@ namespace tpcf {
 
 constexpr float AMBIGUITY = 1.0e-6f;  // > worst fp32 error of the edge position (~1.5e-7 px)
 constexpr float FAST_XMAX = 0.25f;    // |half longitude offset| covered by the polynomial
-constexpr int FLUSH_RINGS = 8;        // rings summed in registers before a shared-memory flush
+constexpr int FLUSH_RINGS = 8;        // default rings summed in registers before a shared-memory flush
 
 __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
     long long q = a / b;
@@ -198,12 +198,11 @@ __device__ __forceinline__ Fold fold_angle(float cph, float sph) {
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
-// acc[m] += (wc cos(m phi), ws sin(m phi)), m = 0..M.
+// acc[m] += (wc cos(m phi), ws sin(m phi)), m = 0..M, from the folded angle.
 template <int M>
-__device__ __forceinline__ void harmonics(float2 (&acc)[M + 1], float cph, float sph, float wc, float ws) {
+__device__ __forceinline__ void harmonicsf(float2 (&acc)[M + 1], const Fold& f, float wc, float ws) {
     acc[0].x += wc;
     if constexpr (M >= 1) {
-        const Fold f = fold_angle(cph, sph);
         float2 X = make_float2(wc * f.ac, ws * f.ss);           // X_1 (psi frame)
         float2 D = make_float2(0.5f * f.lam * wc, ws * f.ss);   // X_1 - X_0
         const float2 S2 = make_float2(f.sg, f.sg);
@@ -218,14 +217,18 @@ __device__ __forceinline__ void harmonics(float2 (&acc)[M + 1], float cph, float
     }
 }
 
-// The same for two pixels a and b at once (two independent chains for
-// instruction-level parallelism).
 template <int M>
-__device__ __forceinline__ void harmonics2(float2 (&acc)[M + 1], float ca, float sa, float wca, float wsa, float cb,
-                                           float sb, float wcb, float wsb) {
+__device__ __forceinline__ void harmonics(float2 (&acc)[M + 1], float cph, float sph, float wc, float ws) {
+    harmonicsf<M>(acc, fold_angle(cph, sph), wc, ws);
+}
+
+// The same for two pixels a and b at once (two independent chains for
+// instruction-level parallelism), from their folded angles.
+template <int M>
+__device__ __forceinline__ void harmonics2f(float2 (&acc)[M + 1], const Fold& fa, float wca, float wsa,
+                                            const Fold& fb, float wcb, float wsb) {
     acc[0].x += wca + wcb;
     if constexpr (M >= 1) {
-        const Fold fa = fold_angle(ca, sa), fb = fold_angle(cb, sb);
         float2 Xa = make_float2(wca * fa.ac, wsa * fa.ss), Da = make_float2(0.5f * fa.lam * wca, wsa * fa.ss);
         float2 Xb = make_float2(wcb * fb.ac, wsb * fb.ss), Db = make_float2(0.5f * fb.lam * wcb, wsb * fb.ss);
         const float2 Sa = make_float2(fa.sg, fa.sg), Sb = make_float2(fb.sg, fb.sg);
@@ -243,6 +246,22 @@ __device__ __forceinline__ void harmonics2(float2 (&acc)[M + 1], float ca, float
                 acc[m] = __fadd2_rn(acc[m], __fadd2_rn(Xa, Xb));
         }
     }
+}
+
+template <int M>
+__device__ __forceinline__ void harmonics2(float2 (&acc)[M + 1], float ca, float sa, float wca, float wsa, float cb,
+                                           float sb, float wcb, float wsb) {
+    harmonics2f<M>(acc, fold_angle(ca, sa), wca, wsa, fold_angle(cb, sb), wcb, wsb);
+}
+
+// A folded angle held by lane `src`, broadcast to the warp.
+__device__ __forceinline__ Fold shfl_fold(const Fold& f, int src) {
+    Fold g;
+    g.ac = __shfl_sync(0xffffffffu, f.ac, src);
+    g.ss = __shfl_sync(0xffffffffu, f.ss, src);
+    g.sg = __shfl_sync(0xffffffffu, f.sg, src);
+    g.lam = __shfl_sync(0xffffffffu, f.lam, src);
+    return g;
 }
 
 // p mod n for -n <= p < 2n (every unwrapped index of a run lies in that range).
@@ -392,6 +411,75 @@ __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const 
     }
 }
 
+// walk_pairs for the case of a belt ring pair (the neighbour ring has as many pixels
+// as the pivot ring): the 32 pivots of the tile then sit at the same fractional
+// position relative to ring r, so every lane's run starts at the same offset from its
+// own pivot and has the same length, and at step t all lanes see a neighbour at the
+// same offset, hence the same position angle.  Each lane computes the (folded) angle of
+// one step of a block of 32 and the warp shares them by shuffles, instead of every lane
+// computing the same angle.  Lane l's pixels are those of lane 0 shifted by l, so the
+// loads of a step stay coalesced.
+template <int M, bool SELF, class L>
+__device__ __forceinline__ void walk_pairs_shared(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
+                                                  int mb, float2 (&acc)[M + 1], float& W, float& Q, float& QW) {
+    if (len <= 0) return;
+    const int lane = threadIdx.x & 31;
+    const float i0 = (float)(a - c.cint);
+    const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
+    const auto row = ld.row(R.first);
+    int ip = wrap_idx(a, R.n);
+    int im_ = wrap_idx(mb - a, R.n);
+    for (int t0 = 0; t0 < len; t0 += 32) {
+        // this lane's step: t0 + lane
+        Fold mine;
+        {
+            const float ft = i0 + (float)(t0 + lane);
+            float cph, sph;
+            if (fabsf(ft - c.cfrac) * R.step <= FAST_XMAX)
+                pixel_dir<true>(ft, xneg, uneg, R, cph, sph);
+            else
+                pixel_dir<false>(ft, xneg, uneg, R, cph, sph);
+            mine = fold_angle(cph, sph);
+        }
+        const int nstep = min(32, len - t0);
+        int tt = 0;
+        for (; tt + 1 < nstep; tt += 2) {
+            const Fold fa = shfl_fold(mine, tt), fb = shfl_fold(mine, tt + 1);
+            const int ip1 = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
+            const int im1 = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
+            const float2 p0 = row(ip), m0 = row(im_), p1 = row(ip1), m1 = row(im1);
+            harmonics2f<M>(acc, fa, p0.x + m0.x, p0.x - m0.x, fb, p1.x + m1.x, p1.x - m1.x);
+            W += (p0.y + m0.y) + (p1.y + m1.y);
+            if (SELF) {
+                Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, fmaf(p1.x, p1.x, fmaf(m1.x, m1.x, Q))));
+                QW = fmaf(p0.y, p0.y, fmaf(m0.y, m0.y, fmaf(p1.y, p1.y, fmaf(m1.y, m1.y, QW))));
+            }
+            ip = ip1 + 1 >= R.n ? ip1 + 1 - R.n : ip1 + 1;
+            im_ = im1 - 1 < 0 ? im1 - 1 + R.n : im1 - 1;
+        }
+        if (tt < nstep) {
+            const Fold fa = shfl_fold(mine, tt);
+            const float2 p0 = row(ip), m0 = row(im_);
+            harmonicsf<M>(acc, fa, p0.x + m0.x, p0.x - m0.x);
+            W += p0.y + m0.y;
+            if (SELF) {
+                Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, Q));
+                QW = fmaf(p0.y, p0.y, fmaf(m0.y, m0.y, QW));
+            }
+            ip = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
+            im_ = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
+        }
+    }
+}
+
+// True when every lane's run has lane 0's start offset and length (belt ring pairs).
+__device__ __forceinline__ bool runs_shared(const LaneC& c, int a, int len) {
+    const int rel = a - c.cint;
+    const int rel0 = __shfl_sync(0xffffffffu, rel, 0), len0 = __shfl_sync(0xffffffffu, len, 0);
+    const unsigned cf = __float_as_uint(c.cfrac), cf0 = __shfl_sync(0xffffffffu, cf, 0);
+    return __all_sync(0xffffffffu, rel == rel0 && len == len0 && cf == cf0);
+}
+
 // Runs of bin k on ring r for the lane's pivot.  Fills up to two runs (a, len) and,
 // in mirror mode, one pair run plus an optional centre pixel.
 struct BinRuns {
@@ -515,6 +603,10 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
                 QW = fmaf(v.y, v.y, QW);
             }
         }
+        if (runs_shared(c, b.a0, b.n0)) {
+            walk_pairs_shared<M, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW);
+            return;
+        }
         const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
         if (fast)
             walk_pairs<M, true, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW);
@@ -555,11 +647,24 @@ __device__ __forceinline__ PivotRing pivot_ring(const MapDev& g, int i) {
     return P;
 }
 
+// Where the tile's moments live in shared memory.  LayKM: A[k][m][re/im][32 pivots],
+// W[k][32], Q[k][32], QW[k][32] (the FP32 contraction and the adjoint read this).
+struct LayKM {
+    float *sA, *sW, *sQ, *sQW;
+    int M1;  // m_max + 1
+    __device__ __forceinline__ float* a(int k, int m, int part, int lane) const {
+        return sA + ((size_t)(k * M1 + m) * 2 + part) * TILE + lane;
+    }
+    __device__ __forceinline__ float* w(int k, int lane) const { return sW + k * TILE + lane; }
+    __device__ __forceinline__ float* q(int k, int lane) const { return sQ + k * TILE + lane; }
+    __device__ __forceinline__ float* qw(int k, int lane) const { return sQW + k * TILE + lane; }
+};
+
 // All warps of the CTA: accumulate the moments of the tile into shared memory.
 // Smem must be zeroed beforehand; it is complete after the caller's __syncthreads().
-template <int M, bool SELF, class L>
-__device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P, int q, const L& ld, float* sA,
-                                             float* sW, float* sQ, float* sQW) {
+template <int M, bool SELF, class L, class Lay>
+__device__ __forceinline__ void tile_moments_l(const MapDev& g, const PivotRing& P, int q, const L& ld,
+                                               const Lay& lay, int flush) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < g.K; ++k) {
         const int2 br = g.bin_range[(long long)P.i * g.K + k];
@@ -568,31 +673,37 @@ __device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P
 #pragma unroll
         for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
         float W = 0.0f, Q = 0.0f, QW = 0.0f;
-        float* a = sA + (size_t)k * (M + 1) * 2 * TILE;
-        // Blocked summation: the registers sum FLUSH_RINGS rings, then the block is
-        // added into shared memory, which keeps the running sums short.
+        // Blocked summation: the registers sum `flush` rings (FLUSH_RINGS unless
+        // tuned), then the block is added into shared memory, which keeps the running
+        // sums short.
         int nr = 0;
         for (int r = br.x + warp; r <= br.y; r += NWARPS) {
             fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, acc, W, Q, QW);
-            if (++nr == FLUSH_RINGS || r + NWARPS > br.y) {
+            if (++nr == flush || r + NWARPS > br.y) {
                 nr = 0;
 #pragma unroll
                 for (int m = 0; m <= M; ++m) {
-                    atomicAdd(a + (2 * m) * TILE + lane, acc[m].x);
-                    atomicAdd(a + (2 * m + 1) * TILE + lane, acc[m].y);
+                    atomicAdd(lay.a(k, m, 0, lane), acc[m].x);
+                    atomicAdd(lay.a(k, m, 1, lane), acc[m].y);
                     acc[m] = make_float2(0.0f, 0.0f);
                 }
-                atomicAdd(sW + k * TILE + lane, W);
+                atomicAdd(lay.w(k, lane), W);
                 W = 0.0f;
                 if (SELF) {
-                    atomicAdd(sQ + k * TILE + lane, Q);
-                    atomicAdd(sQW + k * TILE + lane, QW);
+                    atomicAdd(lay.q(k, lane), Q);
+                    atomicAdd(lay.qw(k, lane), QW);
                     Q = 0.0f;
                     QW = 0.0f;
                 }
             }
         }
     }
+}
+
+template <int M, bool SELF, class L>
+__device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P, int q, const L& ld, float* sA,
+                                             float* sW, float* sQ, float* sQW, int flush) {
+    tile_moments_l<M, SELF>(g, P, q, ld, LayKM{sA, sW, sQ, sQW, M + 1}, flush);
 }
 
 // Per-tile partial sums into the CTA's FP64 slot (eq. zetamEst2 summed over the
@@ -660,54 +771,94 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
 // The contraction of eq. zetamEst2 over a tile's 32 pivots is, for each m, the Gram
 // matrix G = X diag(w d) X^T of X = [Re a ; Im a] (rows r = 2k + part, 32 pivot
 // columns): S_m(k1,k2) = G[2k1][2k2] + G[2k1+1][2k2+1] + i (G[2k1][2k2+1] - G[2k1+1][2k2])
-// in the convention a = re - i im.  D is the same product of the W^k rows with the
-// weights w.  On the 5th-generation tensor cores, per m:
-//   D[128 x N] = A[128 x 32] . B[N x 32]^T,  kind::tf32, FP32 accumulate in TMEM,
-// A = X diag(w d) and B = X in shared memory (K-major, no swizzle: 8-row x 16-byte
-// core matrices, K-adjacent ones 128 B apart, 8-row groups 1024 B apart).  Each
-// operand is split into a tf32 part and its fp32 remainder, and the three products
-// hi.hi + hi.lo + lo.hi run into the same accumulator (TF32x3; the dropped lo.lo term
-// is below 2^-22 relative).  A has 128 rows but only 2K are written: the MMA reads its
-// other rows from whatever follows in shared memory, which only reaches accumulator
-// rows that are never read.  One thread issues; completion is tracked by an mbarrier
-// with a bounded wait; warps 0-1 read the accumulator rows back and add the S and D
-// entries into the CTA's FP64 slot.
-constexpr int TC_TMEM_COLS = 64;              // accumulator columns (N <= 64)
-constexpr int TC_A_WINDOW = 16 * 1024;        // bytes the MMA reads from A (128 rows x 128 B)
+// in the convention a = re - i im; D is the Gram matrix of the W^k rows with the
+// weights w.  On the 5th-generation tensor cores (kind::tf32, FP32 accumulation in
+// tensor memory), per block of rows (each m, then the W block):
+//   * the moments are accumulated straight into the layout the MMA reads: rows of 32
+//     pivots (128 B), 16-byte chunks XOR-swizzled by the row index (the 128-byte
+//     swizzle), blocks starting on 1024-byte boundaries; no operand copy of X exists;
+//   * with Y = X diag(sqrt|w d|) and s = sign(w d), G = Y diag(s) Y^T.  Y is split into
+//     a tf32 part hi (its low 13 mantissa bits cleared, written back in place) and
+//     the fp32 remainder lo, and G = hi s hi^T + C + C^T with C = hi s lo^T (the
+//     dropped lo s lo^T term is below 2^-22 relative): two MMAs per 8-pivot step,
+//     A = hi in place, B = s hi and s lo in a small staging buffer;
+//   * the MMA is 128 x N; rows of A beyond the block come from the following shared
+//     memory and only reach accumulator rows that are never read;
+//   * one thread issues, an mbarrier tracks completion (bounded wait), warps 0-1 read
+//     the two accumulators back, C^T goes through shared memory, and S (or D) is added
+//     into the CTA's FP64 slot.
+// The operands cost no shared memory beyond the moments but the staging buffer, so
+// the kernel keeps the FP32 forward's 3 CTAs per SM at 20 bins and m_max 10.
+constexpr int TC_TMEM_COLS = 128;  // two accumulators of up to 64 columns
 constexpr int ST_TC_TIMEOUT = ST_TC_TIMEOUT_BIT;
 
-__host__ __device__ inline int tc_rows(int K) { return (2 * K + 15) & ~15; }
-__host__ __device__ inline size_t tc_operand_bytes(int K) { return (size_t)tc_rows(K) * 128; }
-// Shared memory of the TC operands (placed first) and the padding that keeps the
-// 16 KB window read from A_lo inside the allocation.
-__host__ __device__ inline size_t tc_region_bytes(int K) { return 4 * tc_operand_bytes(K); }
-__host__ __device__ inline size_t tc_min_total_bytes(int K) { return tc_operand_bytes(K) + TC_A_WINDOW; }
+// Shared-memory plan of the tensor-core forward tile (in floats from a 1024-byte
+// aligned base).
+struct TcLayout {
+    int Rm, RD, NBm, NBd;  // rows per m block and of the W block; MMA N of each
+    int x0, D0;            // first row of the moments; first row of the W block
+    int offB, offPiv, offSc, offQ, offQW;
+    int total;             // floats
+};
+
+__host__ __device__ inline TcLayout tc_layout(int K, int M, bool self) {
+    TcLayout L;
+    L.Rm = (2 * K + 7) & ~7;
+    L.RD = (K + 7) & ~7;
+    L.NBm = (2 * K + 15) & ~15;
+    L.NBd = (K + 15) & ~15;
+    L.x0 = 0;
+    L.D0 = (M + 1) * L.Rm;
+    int off = (L.D0 + L.RD) * TILE;
+    L.offB = off;  // B hi rows, then B lo rows (NBm each); reused for the C^T staging
+    off += 2 * L.NBm * TILE;
+    L.offPiv = off;  // (w d, w) of the pivots
+    off += 2 * TILE;
+    L.offSc = off;  // sqrt|w d|, sign(w d), sqrt w
+    off += 3 * TILE;
+    L.offQ = off;
+    L.offQW = off + (self ? K * TILE : 0);
+    if (self) off += 2 * K * TILE;
+    // the MMA of the last block reads 128 rows from its start
+    const int need = (L.D0 + 128) * TILE;
+    L.total = off > need ? off : need;
+    return L;
+}
+
+// bytes of dynamic shared memory (1 KB of slack for the 1024-byte alignment)
+__host__ __device__ inline size_t tc_smem_bytes(int K, int M, bool self) {
+    return (size_t)tc_layout(K, M, self).total * sizeof(float) + 1024;
+}
+
+// Position of (row r, pivot p) in a 128-byte-swizzled block of 32-float rows.
+__device__ __forceinline__ int sw128(int r, int p) { return r * TILE + ((((p >> 2) ^ (r & 7)) << 2) | (p & 3)); }
+
+struct LaySW {
+    float* sX;
+    float *sQ, *sQW;
+    int Rm, D0;
+    __device__ __forceinline__ float* a(int k, int m, int part, int lane) const {
+        return sX + sw128(m * Rm + 2 * k + part, lane);
+    }
+    __device__ __forceinline__ float* w(int k, int lane) const { return sX + sw128(D0 + k, lane); }
+    __device__ __forceinline__ float* q(int k, int lane) const { return sQ + k * TILE + lane; }
+    __device__ __forceinline__ float* qw(int k, int lane) const { return sQW + k * TILE + lane; }
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// UMMA shared-memory descriptor: start address, leading (K) and stride (M/N) byte
-// offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
-           (1ull << 46);
+// UMMA shared-memory descriptor, K-major, 128-byte swizzle: start address, stride
+// between 8-row groups 1024 B, descriptor version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t tc_sdesc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
 }
 
 // Instruction descriptor: D f32, A and B tf32, both K-major, N, M = 128.
 __device__ __forceinline__ uint32_t tc_idesc(int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// Byte offset of element (row r, pivot p) in a K-major no-swizzle operand.
-__device__ __forceinline__ uint32_t tc_off(int r, int p) {
-    return (uint32_t)((((r >> 3) * 8 + (p >> 2)) << 7) + ((r & 7) << 4) + ((p & 3) << 2));
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
@@ -748,6 +899,16 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Per-CTA tensor-core state: TMEM accumulator base, mbarrier and its phase.
 struct TcState {
     uint32_t tmem;
@@ -780,50 +941,59 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
 }
 
 // The tile's S and D partial sums on the tensor cores (see above); the self-pair
-// diagonals stay on the FP32 pipe.  tcbuf: the operand region (tc_region_bytes).
-template <int M>
-__device__ void tile_contract_tc(int K, const float* sA, const float* sW, const float* sQ, const float* sQW,
-                                 const float* sPiv, double* slot, bool self, float* tcbuf, TcState& tc,
-                                 int* status) {
+// diagonals stay on the FP32 pipe.  Called by every thread; the moments in sX are
+// consumed (truncated in place).
+template <int M, bool SELF>
+__device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, int* status) {
+    const TcLayout L = tc_layout(K, M, SELF);
     const int P = n_pairs_tri(K);
     const int nS = (M + 1) * P;
-    const int R2 = 2 * K;
-    const int opw = (int)(tc_operand_bytes(K) / 4);
-    float* Ahi = tcbuf;
-    float* Alo = Ahi + opw;
-    float* Bhi = Alo + opw;
-    float* Blo = Bhi + opw;
+    float* sX = base;
+    float* Bhi = base + L.offB;
+    const float* sPiv = base + L.offPiv;
+    float* sc = base + L.offSc;  // [0] sqrt|w d|, [1] sign(w d), [2] sqrt w
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int mm = 0; mm <= M + 1; ++mm) {
-        const bool isD = mm == M + 1;  // the D Gram: rows W^k, weights w
-        const int rows = isD ? K : R2;
-        const int Nn = (rows + 15) & ~15;
-        for (int e = threadIdx.x; e < Nn * TILE; e += NTHREADS) {
-            // consecutive threads write consecutive words of the core-matrix layout
-            const int r = ((e >> 8) << 3) + ((e >> 2) & 7);
-            const int p = (((e >> 5) & 7) << 2) + (e & 3);
-            float x = 0.0f;
-            if (r < rows)
-                x = isD ? sW[r * TILE + p] : sA[((size_t)((r >> 1) * (M + 1) + mm) * 2 + (r & 1)) * TILE + p];
-            const float a = x * (isD ? sPiv[TILE + p] : sPiv[p]);
-            const float ah = tf32_rna(a), xh = tf32_rna(x);
-            Ahi[e] = ah;
-            Alo[e] = a - ah;
-            Bhi[e] = xh;
-            Blo[e] = x - xh;
+    if (threadIdx.x < TILE) {
+        const float wd = sPiv[lane], w = sPiv[TILE + lane];
+        sc[lane] = sqrtf(fabsf(wd));
+        sc[TILE + lane] = wd < 0.0f ? -1.0f : 1.0f;
+        sc[2 * TILE + lane] = sqrtf(w);
+    }
+    __syncthreads();
+    for (int b = 0; b <= M + 1; ++b) {
+        const bool isD = b == M + 1;
+        const int rows = isD ? K : 2 * K;
+        const int N = isD ? L.NBd : L.NBm;
+        const int r0 = isD ? L.D0 : b * L.Rm;
+        float* Blo = Bhi + N * TILE;
+        // split the block: hi in place, (s hi, s lo) into the staging rows; rows of B
+        // beyond the block are zero
+        for (int e = threadIdx.x; e < N * TILE; e += NTHREADS) {
+            const int i = e >> 5, cp = e & 31;
+            const int p = (((cp >> 2) ^ (i & 7)) << 2) | (cp & 3);  // r0 is a multiple of 8
+            float bh = 0.0f, bl = 0.0f;
+            if (i < rows) {
+                const float x = sX[(r0 + i) * TILE + cp] * (isD ? sc[2 * TILE + p] : sc[p]);
+                const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+                const float sg = isD ? 1.0f : sc[TILE + p];
+                sX[(r0 + i) * TILE + cp] = hi;
+                bh = sg * hi;
+                bl = sg * (x - hi);
+            }
+            Bhi[e] = bh;
+            Blo[e] = bl;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t idesc = tc_idesc(Nn);
-            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+            const uint32_t idesc = tc_idesc(N);
+            const uint32_t a0 = smem_u32(sX + r0 * TILE), bh = smem_u32(Bhi), bl = smem_u32(Blo);
 #pragma unroll
             for (int k8 = 0; k8 < TILE / 8; ++k8) {
-                const uint32_t o = (uint32_t)k8 * 256u;  // two K-adjacent core matrices per k-step
-                tc_mma(tc.tmem, tc_sdesc(ah + o), tc_sdesc(bh + o), idesc, k8 > 0);
-                tc_mma(tc.tmem, tc_sdesc(ah + o), tc_sdesc(bl + o), idesc, 1);
-                tc_mma(tc.tmem, tc_sdesc(al + o), tc_sdesc(bh + o), idesc, 1);
+                const uint32_t o = (uint32_t)k8 * 32u;  // 8 tf32 pivots per MMA
+                tc_mma(tc.tmem, tc_sdesc_sw128(a0 + o), tc_sdesc_sw128(bh + o), idesc, k8 > 0);
+                tc_mma(tc.tmem + (uint32_t)L.NBm, tc_sdesc_sw128(a0 + o), tc_sdesc_sw128(bl + o), idesc, k8 > 0);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              tc.mbar)
@@ -837,32 +1007,50 @@ __device__ void tile_contract_tc(int K, const float* sA, const float* sW, const 
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (*tc.fail) return;
+        // C rows into the staging area (the B rows are no longer read): Cst[r][c]
+        float* Cst = Bhi;
+        const int r = warp * 32 + lane;
         if (warp * 32 < rows) {
-            const int r = warp * 32 + lane;
-            for (int c0 = 0; c0 < Nn; c0 += 16) {
-                float v[16];
-                tc_ld16(tc.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            for (int c0 = 0; c0 < N; c0 += 8) {
+                float v[8];
+                tc_ld8(tc.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L.NBm + c0), v);
+                if (r < rows) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) Cst[r * N + c0 + j] = v[j];
+                }
+            }
+        }
+        __syncthreads();
+        if (warp * 32 < rows) {
+            for (int c0 = 0; c0 < N; c0 += 8) {
+                float gv[8];
+                tc_ld8(tc.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, gv);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int s2 = c0 + j;
+                    if (r < rows && s2 < rows) gv[j] += Cst[r * N + s2] + Cst[s2 * N + r];
+                }
                 if (isD) {
                     if (r < K) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < 8; ++j) {
                             const int k2 = c0 + j;
-                            if (k2 >= r && k2 < K) atomicAdd(slot + 2 * nS + k2 * (k2 + 1) / 2 + r, (double)v[j]);
+                            if (k2 >= r && k2 < K) atomicAdd(slot + 2 * nS + k2 * (k2 + 1) / 2 + r, (double)gv[j]);
                         }
                     }
                 } else {
-                    float u[16];
+                    float u[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) u[j] = __shfl_down_sync(0xffffffffu, v[j], 1);
-                    if ((r & 1) == 0 && r < R2) {
+                    for (int j = 0; j < 8; ++j) u[j] = __shfl_down_sync(0xffffffffu, gv[j], 1);
+                    if ((r & 1) == 0 && r < rows) {
                         const int k1 = r >> 1;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < 4; ++j) {
                             const int k2 = (c0 >> 1) + j;
                             if (k2 >= k1 && k2 < K) {
-                                const int e = mm * P + k2 * (k2 + 1) / 2 + k1;
-                                atomicAdd(slot + 2 * e, (double)(v[2 * j] + u[2 * j + 1]));
-                                atomicAdd(slot + 2 * e + 1, (double)(v[2 * j + 1] - u[2 * j]));
+                                const int e = b * P + k2 * (k2 + 1) / 2 + k1;
+                                atomicAdd(slot + 2 * e, (double)(gv[2 * j] + u[2 * j + 1]));
+                                atomicAdd(slot + 2 * e + 1, (double)(gv[2 * j + 1] - u[2 * j]));
                             }
                         }
                     }
@@ -872,9 +1060,11 @@ __device__ void tile_contract_tc(int K, const float* sA, const float* sW, const 
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
-    if (self) {
+    if (SELF) {
         const float* wd = sPiv;
         const float* wt = sPiv + TILE;
+        const float* sQ = base + L.offQ;
+        const float* sQW = base + L.offQW;
         for (int k = threadIdx.x; k < K; k += NTHREADS) {
             float s1 = 0.0f, s2 = 0.0f;
             for (int j = 0; j < TILE; ++j) {
@@ -889,9 +1079,8 @@ __device__ void tile_contract_tc(int K, const float* sA, const float* sW, const 
 
 // One forward tile: the moments of its 32 pivots, then their partial sums added to
 // the CTA's slot.  Called by every thread of the CTA (contains barriers).
-template <int M, bool SELF, bool DIRECT, bool TC = false>
-__device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem,
-                                         float* tcbuf = nullptr, TcState* tc = nullptr) {
+template <int M, bool SELF, bool DIRECT>
+__device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem) {
     const int K = g.K;
     float* sA = smem;
     float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
@@ -923,36 +1112,79 @@ __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int 
     }
     __syncthreads();
     if (DIRECT)
-        tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW);
+        tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW, c.flush);
     else
-        tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
+        tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush);
     __syncthreads();
-    if constexpr (TC)
-        tile_contract_tc<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF, tcbuf, *tc, c.status);
-    else
-        tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+    tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
     __syncthreads();
 }
 
-template <int M, bool SELF, bool DIRECT>
-__global__ void __launch_bounds__(NTHREADS, 3) map_fwd_kernel(MapDev g, MapCall c) {
+// One forward tile with the tensor-core contraction: the moments accumulate in the
+// swizzled layout of tc_layout(), then tile_contract_tc.
+template <int M, bool SELF>
+__device__ __forceinline__ void fwd_tile_tc(const MapDev& g, const MapCall& c, int tile, double* slot, float* base,
+                                            TcState& tc) {
+    const int K = g.K;
+    const int lane = threadIdx.x & 31;
+    const int2 tq = g.tiles[tile];
+    if (tq.x < 0 || tq.x >= g.nrings) {
+        if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
+        __syncthreads();
+        return;
+    }
+    const PivotRing P = pivot_ring(g, tq.x);
+    const int q = tq.y + lane;
+    const long long pix = g.ring_first[P.i] + q;
+    const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+    float2 pv = make_float2(0.0f, 0.0f);
+    if (in) pv = c.wdw[pix];
+    const int qg = min(q, P.n_i - 1);
+    if (!__syncthreads_or(pv.y != 0.0f)) return;
+    {
+        const TcLayout L = tc_layout(K, M, SELF);
+        const int nx = (L.D0 + L.RD) * TILE;
+        for (int e = threadIdx.x; e < nx; e += NTHREADS) base[e] = 0.0f;
+        if (SELF)
+            for (int e = threadIdx.x; e < 2 * K * TILE; e += NTHREADS) base[L.offQ + e] = 0.0f;
+        if (threadIdx.x < TILE) {
+            base[L.offPiv + lane] = pv.x;
+            base[L.offPiv + TILE + lane] = pv.y;
+        }
+    }
+    __syncthreads();
+    {
+        const int Rm = (2 * K + 7) & ~7, D0 = (M + 1) * Rm;
+        const TcLayout L = tc_layout(K, M, SELF);
+        tile_moments_l<M, SELF>(g, P, qg, PackedLoad{c.wdw}, LaySW{base, base + L.offQ, base + L.offQW, Rm, D0},
+                                c.flush);
+    }
+    __syncthreads();
+    tile_contract_tc<M, SELF>(K, base, slot, tc, c.status);
+    __syncthreads();
+}
+
+// OCC: CTAs per SM the register allocation is sized for (3: 80 registers, 2: 128);
+// the autotuner picks the variant and the grid.
+template <int M, bool SELF, bool DIRECT, int OCC = 3>
+__global__ void __launch_bounds__(NTHREADS, OCC) map_fwd_kernel(MapDev g, MapCall c) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
     double* slot = c.slots + (size_t)blockIdx.x * n_entries(g.K, M);
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
         __syncthreads();
-        const int tile = s_tile;
-        if ((long long)tile >= g.ntiles) break;
-        fwd_tile<M, SELF, DIRECT>(g, c, tile, slot, smem);
+        const long long tile = c.tile_lo + s_tile;
+        if (tile >= c.tile_hi) break;
+        fwd_tile<M, SELF, DIRECT>(g, c, (int)tile, slot, smem);
     }
 }
 
-// The forward with the tensor-core contraction: the dynamic shared memory starts
-// with the operand region (tc_region_bytes), the tile's arrays follow.
+// The forward with the tensor-core contraction (3 CTAs per SM where the shared
+// memory allows it; 128 accumulator columns each, so at most 4 fit an SM's TMEM).
 template <int M, bool SELF>
-__global__ void __launch_bounds__(NTHREADS, 2) map_fwd_tc_kernel(MapDev g, MapCall c) {
-    extern __shared__ __align__(16) float smem_tc[];
+__global__ void __launch_bounds__(NTHREADS, 3) map_fwd_tc_kernel(MapDev g, MapCall c) {
+    extern __shared__ __align__(1024) float smem_tc[];
     __shared__ int s_tile;
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
@@ -960,15 +1192,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_tc_kernel(MapDev g, MapCa
     if (threadIdx.x == 0) s_fail = 0;
     tc_setup(&s_tmem, &s_mbar);
     TcState tc{s_tmem, smem_u32(&s_mbar), 0u, &s_fail};
-    float* tcbuf = smem_tc;
-    float* tile_smem = smem_tc + tc_region_bytes(g.K) / 4;
+    // 1024-byte aligned base of the swizzled blocks
+    const uint32_t mis = smem_u32(smem_tc) & 1023u;
+    float* base = smem_tc + (mis ? (1024u - mis) / 4 : 0u);
     double* slot = c.slots + (size_t)blockIdx.x * n_entries(g.K, M);
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
         __syncthreads();
-        const int tile = s_tile;
-        if ((long long)tile >= g.ntiles || s_fail) break;
-        fwd_tile<M, SELF, false, true>(g, c, tile, slot, tile_smem, tcbuf, &tc);
+        const long long tile = c.tile_lo + s_tile;
+        if (tile >= c.tile_hi || s_fail) break;
+        fwd_tile_tc<M, SELF>(g, c, (int)tile, slot, base, tc);
     }
     tc_teardown(s_tmem);
 }
@@ -1007,9 +1240,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) batch_fwd_kernel(const BatchItem*
 // Uses the same run construction as the forward, without touching pixel data.
 __global__ void __launch_bounds__(NTHREADS) map_count_kernel(MapDev g, const float2* __restrict__ wdw,
                                                              long long piv_lo, long long piv_hi,
+                                                             long long tile_lo, long long tile_hi,
                                                              unsigned long long* counts) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    for (long long tile = tile_lo + blockIdx.x; tile < tile_hi; tile += gridDim.x) {
         const int2 tq = g.tiles[tile];
         const PivotRing P = pivot_ring(g, tq.x);
         const int q = tq.y + lane;
@@ -1066,12 +1300,11 @@ constexpr int ROW = 512;  // floats per warp row buffer (wider rows fall back to
 // the recurrence of harmonics(); even and odd multipoles are summed apart and the odd
 // sum takes the sign sigma at the end.
 template <int M>
-__device__ __forceinline__ void adj_harmonics(const float2 (&h)[M + 1], float cph, float sph, float& X, float& Y) {
+__device__ __forceinline__ void adj_harmonicsf(const float2 (&h)[M + 1], const Fold& f, float& X, float& Y) {
     float2 ev = make_float2(h[0].x, 0.0f);
     float2 od = make_float2(0.0f, 0.0f);
     float sg = 1.0f;
     if constexpr (M >= 1) {
-        const Fold f = fold_angle(cph, sph);
         sg = f.sg;
         float2 T = make_float2(f.ac, f.ss);
         float2 D = make_float2(0.5f * f.lam, f.ss);
@@ -1089,6 +1322,11 @@ __device__ __forceinline__ void adj_harmonics(const float2 (&h)[M + 1], float cp
     }
     X = fmaf(sg, od.x, ev.x);
     Y = fmaf(sg, od.y, ev.y);
+}
+
+template <int M>
+__device__ __forceinline__ void adj_harmonics(const float2 (&h)[M + 1], float cph, float sph, float& X, float& Y) {
+    adj_harmonicsf<M>(h, fold_angle(cph, sph), X, Y);
 }
 
 // Where the contribution to pixel p (unwrapped index on ring R) goes.
@@ -1109,13 +1347,12 @@ __device__ __forceinline__ void sink_add(const RowSink& s, int p_unwrapped, int 
 }
 
 template <int M>
-__device__ __forceinline__ void adj_harmonics2(const float2 (&h)[M + 1], float ca, float sa, float cb, float sb,
-                                               float& Xa, float& Ya, float& Xb, float& Yb) {
+__device__ __forceinline__ void adj_harmonics2f(const float2 (&h)[M + 1], const Fold& fa, const Fold& fb, float& Xa,
+                                                float& Ya, float& Xb, float& Yb) {
     float2 eva = make_float2(h[0].x, 0.0f), evb = eva;
     float2 oda = make_float2(0.0f, 0.0f), odb = oda;
     float sga = 1.0f, sgb = 1.0f;
     if constexpr (M >= 1) {
-        const Fold fa = fold_angle(ca, sa), fb = fold_angle(cb, sb);
         sga = fa.sg;
         sgb = fb.sg;
         float2 Ta = make_float2(fa.ac, fa.ss), Da = make_float2(0.5f * fa.lam, fa.ss);
@@ -1142,6 +1379,12 @@ __device__ __forceinline__ void adj_harmonics2(const float2 (&h)[M + 1], float c
     Ya = fmaf(sga, oda.y, eva.y);
     Xb = fmaf(sgb, odb.x, evb.x);
     Yb = fmaf(sgb, odb.y, evb.y);
+}
+
+template <int M>
+__device__ __forceinline__ void adj_harmonics2(const float2 (&h)[M + 1], float ca, float sa, float cb, float sb,
+                                               float& Xa, float& Ya, float& Xb, float& Yb) {
+    adj_harmonics2f<M>(h, fold_angle(ca, sa), fold_angle(cb, sb), Xa, Ya, Xb, Yb);
 }
 
 template <int M, bool FAST, bool SELF = false>
@@ -1208,6 +1451,54 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
         }
         ip = ip1 + 1 >= R.n ? ip1 + 1 - R.n : ip1 + 1;
         im_ = im1 - 1 < 0 ? im1 - 1 + R.n : im1 - 1;
+    }
+}
+
+// adj_pairs for a belt ring pair, with the position angles shared across the warp
+// (see walk_pairs_shared).
+template <int M, bool SELF = false>
+__device__ __forceinline__ void adj_pairs_shared(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
+                                                 int a, int len, int mb, const float2 (&h)[M + 1], float wdi,
+                                                 const RowSink& s, float ck = 0.0f) {
+    if (len <= 0) return;
+    const int lane = threadIdx.x & 31;
+    const float i0 = (float)(a - c.cint);
+    const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
+    int ip = wrap_idx(a, R.n);
+    int im_ = wrap_idx(mb - a, R.n);
+    const float2* row = wdw + R.first;
+    for (int t0 = 0; t0 < len; t0 += 32) {
+        Fold mine;
+        {
+            const float ft = i0 + (float)(t0 + lane);
+            float cph, sph;
+            if (fabsf(ft - c.cfrac) * R.step <= FAST_XMAX)
+                pixel_dir<true>(ft, xneg, uneg, R, cph, sph);
+            else
+                pixel_dir<false>(ft, xneg, uneg, R, cph, sph);
+            mine = fold_angle(cph, sph);
+        }
+        const int nstep = min(32, len - t0);
+        for (int tt = 0; tt < nstep; tt += 2) {
+            const int t = t0 + tt;
+            const bool two = tt + 1 < nstep;
+            const Fold fa = shfl_fold(mine, tt), fb = shfl_fold(mine, two ? tt + 1 : tt);
+            const int ip1 = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
+            const int im1 = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
+            const float2 p0 = __ldg(row + ip), m0 = __ldg(row + im_);
+            const float2 p1 = two ? __ldg(row + ip1) : make_float2(0.0f, 0.0f);
+            const float2 m1 = two ? __ldg(row + im1) : make_float2(0.0f, 0.0f);
+            float Xa, Ya, Xb, Yb;
+            adj_harmonics2f<M>(h, fa, fb, Xa, Ya, Xb, Yb);
+            sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya + (SELF ? ck * p0.x : 0.0f)));
+            sink_add(s, mb - a - t, im_, wdi * m0.y * (Xa - Ya + (SELF ? ck * m0.x : 0.0f)));
+            if (two) {
+                sink_add(s, a + t + 1, ip1, wdi * p1.y * (Xb + Yb + (SELF ? ck * p1.x : 0.0f)));
+                sink_add(s, mb - a - t - 1, im1, wdi * m1.y * (Xb - Yb + (SELF ? ck * m1.x : 0.0f)));
+            }
+            ip = ip1 + 1 >= R.n ? ip1 + 1 - R.n : ip1 + 1;
+            im_ = im1 - 1 < 0 ? im1 - 1 + R.n : im1 - 1;
+        }
     }
 }
 
@@ -1280,11 +1571,15 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
                 if (SELF) X = fmaf(ck, v.x, X);
                 sink_add(s, p, pw, wdi * v.y * (X + Y));
             }
-            const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
-            if (fast)
-                adj_pairs<M, true, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
-            else
-                adj_pairs<M, false, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
+            if (runs_shared(c, b.a0, b.n0)) {
+                adj_pairs_shared<M, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
+            } else {
+                const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
+                if (fast)
+                    adj_pairs<M, true, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
+                else
+                    adj_pairs<M, false, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
+            }
         } else {
             const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
             const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
@@ -1360,7 +1655,7 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
     }
     __syncthreads();
     // phase 1: the tile's moments, exactly as in the forward
-    tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW);
+    tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush);
     __syncthreads();
     // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
     for (int m = 0; m <= M; ++m) {
@@ -1413,16 +1708,16 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
     __syncthreads();
 }
 
-template <int M, bool SELF>
-__global__ void __launch_bounds__(NTHREADS, 3) map_bwd_kernel(MapDev g, MapCall c) {
+template <int M, bool SELF, int OCC = 3>
+__global__ void __launch_bounds__(NTHREADS, OCC) map_bwd_kernel(MapDev g, MapCall c) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
         __syncthreads();
-        const int tile = s_tile;
-        if ((long long)tile >= g.ntiles) break;
-        bwd_tile<M, SELF>(g, c, tile, smem);
+        const long long tile = c.tile_lo + s_tile;
+        if (tile >= c.tile_hi) break;
+        bwd_tile<M, SELF>(g, c, (int)tile, smem);
     }
 }
 

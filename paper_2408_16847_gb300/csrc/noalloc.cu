@@ -135,6 +135,9 @@ extern "C" tpcf_status tpcf_forward_noalloc(tpcf_plan plan, const float* d_delta
     c.counter = counter;
     c.status = plan->status;
     c.self_subtract = 0;
+    c.flush = plan->tune_fwd.flush;
+    c.tile_lo = 0;  // every tile; those without a pivot in range return at once
+    c.tile_hi = plan->map.ntiles;
     TRY_CUDA(kDirect[plan->M](plan->map, c, grid, s));
     reduce_slots_kernel<<<(plan->nent + 127) / 128, 128, 0, s>>>(slots, grid, plan->nent, sums);
     const int nout = (plan->M + 1) * plan->K * plan->K;

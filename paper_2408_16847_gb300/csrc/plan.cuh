@@ -39,6 +39,14 @@ struct tpcf_plan_s {
     std::vector<void*> allocs;  // everything freed by destroy
     MapDev map{};
     tpcf::CatDev cat{};
+    std::vector<int64_t> tile_off_h;  // map plans: first tile of each ring (host copy)
+    // launch configuration of the map pair kernels (defaults, or picked by the autotuner):
+    // register variant (CTAs per SM the registers are sized for), CTAs per SM launched,
+    // rings summed in registers per shared-memory flush
+    struct Tune {
+        int variant = 3, ctas = 0, flush = 8;
+    } tune_fwd, tune_bwd;
+    bool tuned = false;
     // per-call scratch
     float2* wdw = nullptr;
     double* slots = nullptr;

@@ -79,6 +79,8 @@ struct MapCall {
     const float* H;         // backward: [(M+1) * K * K * 2] fp32, conj(C(k,k')) + C(k',k)
     float* grad;            // backward: [npix]
     int self_subtract;      // subtract the j = k self term
+    int flush;              // rings summed in registers before a shared-memory flush (tuned)
+    int64_t tile_lo, tile_hi;  // tiles that can hold a pivot of [piv_lo, piv_hi)
 };
 
 // One plan of a batch (device-resident): its geometry, its per-call arguments and

@@ -140,6 +140,36 @@ class Plan:
               "tpcf_count_pairs")
         return tuple(int(v) for v in out.cpu())
 
+    def autotune(self, delta: torch.Tensor, w: torch.Tensor, forward: bool = True, adjoint: bool = True,
+                 stream=None) -> dict:
+        """Pick the pair kernels' launch configuration on this device (tpcf_plan_autotune);
+        returns it (see launch_config)."""
+        _need(delta, torch.float32, self.npoints, "delta")
+        _need(w, torch.float32, self.npoints, "w")
+        passes = (1 if forward else 0) | (2 if adjoint else 0)
+        check(lib().tpcf_plan_autotune(self._h, _ptr(delta), _ptr(w), passes, _stream_ptr(stream)),
+              "tpcf_plan_autotune")
+        return self.launch_config()
+
+    def launch_config(self) -> dict:
+        c = (ctypes.c_int32 * 6)()
+        check(lib().tpcf_plan_launch_config(self._h, c), "tpcf_plan_launch_config")
+        return {"forward": {"variant": c[0], "ctas_per_sm": c[1], "flush_rings": c[2]},
+                "adjoint": {"variant": c[3], "ctas_per_sm": c[4], "flush_rings": c[5]}}
+
+    def set_launch_config(self, cfg: dict) -> None:
+        f, b = cfg["forward"], cfg["adjoint"]
+        c = (ctypes.c_int32 * 6)(f["variant"], f["ctas_per_sm"], f["flush_rings"], b["variant"], b["ctas_per_sm"],
+                                 b["flush_rings"])
+        check(lib().tpcf_plan_set_launch_config(self._h, c), "tpcf_plan_set_launch_config")
+
+    def halo(self, begin: int, end: int) -> Tuple[int, int]:
+        """Pixel range of the pivots that can have a neighbour in [begin, end) (map plans)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().tpcf_plan_halo(self._h, int(begin), int(end), ctypes.byref(a), ctypes.byref(b)),
+              "tpcf_plan_halo")
+        return int(a.value), int(b.value)
+
     def run_host(self, delta: np.ndarray, w: np.ndarray, dL_dzeta: Optional[np.ndarray] = None,
                  stream=None):
         """End-to-end on host (pinned or pageable) float32 arrays; returns numpy

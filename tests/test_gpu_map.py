@@ -232,3 +232,34 @@ def test_gradient_with_self_pair_subtraction(nside, M):
         dm = d.copy(); dm[p] -= 1.0
         fd = (L(dp) - L(dm)) / 2.0
         assert abs(fd - grad[p]) <= 1e-3 * np.abs(gref).max(), (p, fd, grad[p])
+
+
+def test_halo_makes_the_adjoint_slice_exact(cuda_device):
+    """tpcf_plan_halo: the pivots of the halo of a pixel slice hold every pivot with a
+    neighbour in the slice (checked by brute force on the pixel centres), and the
+    adjoint over the halo pivots equals the full adjoint on the slice."""
+    tpcf = _tpcf()
+    nside, M = 16, 6
+    edges = list(np.geomspace(1.53, 12.1, 5))
+    K = len(edges) - 1
+    d32, w32 = _case(nside, 400, (2.0, 8.0), synth.BASE_SEED + 71)
+    plan = tpcf.Plan.map(nside, edges, M)
+    npix = 12 * nside * nside
+    xyz = oracle.pix2vec_ring(nside)
+    c = 2 * np.sin(np.deg2rad(edges[-1]) / 2)
+    dt, wt = to_dev(d32), to_dev(w32)
+    _, norm = plan.forward(dt, wt)
+    cot = synth.rng(72).standard_normal((M + 1, K, K))
+    g = torch.zeros((M + 1, K, K, 2), dtype=torch.float64, device=dt.device)
+    g[..., 0] = torch.from_numpy(cot).to(dt.device)
+    full = plan.backward(dt, wt, norm, g).cpu().numpy()
+    for lo, hi in [(0, 300), (1000, 1700), (npix // 2 - 64, npix // 2 + 64), (npix - 500, npix)]:
+        a, b = plan.halo(lo, hi)
+        d2 = ((xyz[:, None, :] - xyz[None, lo:hi, :]) ** 2).sum(-1)
+        near = np.nonzero((d2 < c * c).any(axis=1))[0]
+        assert a <= near.min() and b >= near.max() + 1 and a <= lo and b >= hi
+        part = plan.backward(dt, wt, norm, g, (a, b)).cpu().numpy()
+        scale = np.abs(full[lo:hi]).max()
+        assert np.abs(part[lo:hi] - full[lo:hi]).max() <= 1e-6 * scale
+    assert plan.halo(5, 5) == (5, 5)
+    plan.close()
