@@ -168,9 +168,26 @@ def sm_count(dev=None):
                .multi_processor_count)
 
 
+_PEAK = {}
+
+
 def fp32_peak_tflops(clk, sms):
-    """FP32-pipe peak: SMs x 128 lanes x 2 flops (FMA) x the maximum SM clock."""
+    """FP32-pipe peak: the larger of the two FMA throughputs measured on this GPU by the
+    library's probe (scalar FMA, packed f32x2 FMA), if measured; else SMs x 128 lanes x 2
+    flops x the maximum SM clock."""
+    if _PEAK.get("measured"):
+        return max(_PEAK["measured"])
+    return fp32_peak_derived(clk, sms)
+
+
+def fp32_peak_derived(clk, sms):
     return sms * FP32_LANES_PER_SM * 2 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+
+
+def measure_fp32_peak():
+    from paper_2408_16847_gb300 import tpcf
+    _PEAK["measured"] = tpcf.probe_fp32_peak()
+    return _PEAK["measured"]
 
 
 # --------------------------------------------------------------- GPU clocks
@@ -280,7 +297,8 @@ def oracle_sample_catalog(xu, du, wu, edges, M, n_piv: int):
 def autotune(args, plan, d_dev, w_dev):
     """The plan's launch configuration, picked by the library's autotuner on this GPU
     (set-up, outside the timed region; cached in TPCF_AUTOTUNE_CACHE when set)."""
-    if not args.autotune:
+    if not args.autotune or args.contract == "tc":
+        # the tensor-core forward has a single configuration (3 CTAs per SM)
         return dict(plan.launch_config(), autotuned=False)
     t0 = time.time()
     cfg = plan.autotune(d_dev, w_dev)
@@ -321,6 +339,11 @@ def setup_map(args, dev, rank):
         n = wl.nside
         first = 2 * n * (n - 1) + 4 * n * ((5 * n) // 4 - n)
         piv = (first, first + 4 * n * args.profile_band)
+    elif args.profile_cap:
+        # pivots of the first `profile_cap` rings of the north polar cap (ring r holds 4r
+        # pixels): the cap's kernels alone (not a bench number)
+        r = min(args.profile_cap, wl.nside - 1)
+        piv = (0, 2 * r * (r + 1))
     total, n_sym, n_single = plan.count_pairs(w_dev, piv)
     tune = autotune(args, plan, d_dev, w_dev)
     state = {}
@@ -394,7 +417,7 @@ def setup_map(args, dev, rank):
                 "achieved_implemented": fwd_impl / (ms * 1e-3) / 1e12,
                 "implemented_note": "flops of the implemented loop (mirror pairs share one angle "
                                     "and one recurrence)",
-                "peak_note": "SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
+                "peak_note": "measured FMA throughput (tpcf_probe_fp32_peak, the larger of scalar and f32x2)",
                 "traffic": traffic_per_launch("map_fwd_kernel", 12 * wl.nside ** 2),
                 "traffic_note": "DRAM bytes per launch scaled by pixels from the Nside 512 ncu capture "
                                 "(null when the kernel changed since)"}
@@ -415,15 +438,16 @@ def setup_map(args, dev, rank):
               "m_max": M, "pass": "forward + adjoint" if headline_both else "forward",
               "pairs_per_step_per_gpu": total,
               "contraction": "tensor cores, TF32x3" if args.contract == "tc" else "FP32 pipe",
-              "pivots": "all" if piv is None else "profile band: %d rings from z = 1/2 (%d pivots)" % (
-                  args.profile_band, piv[1] - piv[0]),
+              "pivots": "all" if piv is None else ("profile band: %d rings from z = 1/2 (%d pivots)" % (
+                  args.profile_band, piv[1] - piv[0]) if args.profile_band else
+                  "profile cap: %d rings from the north pole (%d pivots)" % (args.profile_cap, piv[1] - piv[0])),
               "l2": "inputs larger than L2 (%.2f GB of (w d, w) per map)" % (8 * 12 * wl.nside ** 2 / 1e9)
               if 12 * wl.nside ** 2 * 8 > 129e6 else "L2 flushed between steps",
               "parallelism": "independent map per GPU", "launch_config": tune}
     W = dict(step=step_fb if headline_both else step_fwd,
              split=("forward", "adjoint") if headline_both else ("forward", None),
              pairs=total, e2e=e2e_step, e2e_bytes=(in_bytes, out_bytes),
-             vs_baseline=PAPER_FWD_PAIRS_PER_S.get(wl.name) if (not headline_both and not args.profile_band) else None,
+             vs_baseline=PAPER_FWD_PAIRS_PER_S.get(wl.name) if (not headline_both and piv is None) else None,
              launches=plan.kernel_launches, config=config, cpu_baseline=cpu_baseline,
              small_l2=12 * wl.nside ** 2 * 8 <= 129e6, close=plan.close)
     if headline_both:
@@ -687,6 +711,8 @@ def run_gpu(args):
         raise SystemExit("unknown workload " + args.workload)
     stream = torch.cuda.current_stream()
     sms = sm_count(dev)
+    peak_meas = measure_fp32_peak()
+    log("[rank %d] FP32 FMA throughput: %.1f TFLOP/s scalar, %.1f TFLOP/s f32x2" % (rank, *peak_meas))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if W["small_l2"] else None
     gpu_id = str(local)
     try:
@@ -814,6 +840,9 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk,
             "sm_count": sms,
+            "fp32_peak": {"scalar_fma_tflops": peak_meas[0], "f32x2_fma_tflops": peak_meas[1],
+                          "derived_tflops": fp32_peak_derived(clk, sms),
+                          "note": "measured by tpcf_probe_fp32_peak on this GPU; roofline peaks use the larger"},
             "cpu_baseline": cpu,
             "parity": parity,
         }
@@ -875,6 +904,9 @@ def main():
     ap.add_argument("--profile-band", type=int, default=0,
                     help="map workloads: restrict the pivots to this many belt rings from z = 1/2 "
                          "(for ncu captures of full-resolution kernels; not a bench configuration)")
+    ap.add_argument("--profile-cap", type=int, default=0,
+                    help="map workloads: restrict the pivots to this many rings from the north pole "
+                         "(timing of the polar-cap kernels; not a bench configuration)")
     ap.add_argument("--pass", dest="pass_", default="auto", choices=["auto", "both", "forward"],
                     help="map workloads: the timed step is the forward (full-sky maps) or the forward + "
                          "adjoint (the masked map) by default")

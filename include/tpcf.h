@@ -276,6 +276,14 @@ tpcf_status tpcf_plan_sync(tpcf_plan plan);
 void tpcf_plan_destroy(tpcf_plan plan);
 
 /*
+ * FP32-pipe throughput of the current device, measured (no counterpart in the paper; the
+ * denominator of the pair kernels' roofline): tflops[0] with scalar FMAs, tflops[1] with
+ * packed two-lane FMAs (f32x2), each the best of three timed launches of 8 x SMs CTAs.
+ * Host output double[2]; synchronises `stream`; allocates a small temporary.
+ */
+tpcf_status tpcf_probe_fp32_peak(double* tflops, void* stream);
+
+/*
  * Test hooks for the error paths (no counterpart in the paper).
  * tpcf_test_fail_allocation(n): the n-th device allocation the library attempts from
  * now on fails as if the device were out of memory (the calls above then return

@@ -24,7 +24,8 @@ EXPORTS = ["tpcf_status_string", "tpcf_last_error", "tpcf_plan_create_map", "tpc
            "tpcf_plan_npoints", "tpcf_plan_kernel_launches", "tpcf_forward", "tpcf_forward_noalloc", "tpcf_backward", "tpcf_count_pairs", "tpcf_run_host", "tpcf_batch_create",
            "tpcf_batch_launch", "tpcf_batch_kernel_launches", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync", "tpcf_normalize",
            "tpcf_plan_destroy", "tpcf_test_fail_allocation", "tpcf_test_live_allocations",
-           "tpcf_plan_halo", "tpcf_plan_autotune", "tpcf_plan_launch_config", "tpcf_plan_set_launch_config"]
+           "tpcf_plan_halo", "tpcf_plan_autotune", "tpcf_plan_launch_config", "tpcf_plan_set_launch_config",
+           "tpcf_probe_fp32_peak"]
 
 
 class TpcfError(RuntimeError):
@@ -98,6 +99,8 @@ def lib() -> ctypes.CDLL:
     L.tpcf_plan_launch_config.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
     L.tpcf_plan_set_launch_config.restype = ctypes.c_int
     L.tpcf_plan_set_launch_config.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+    L.tpcf_probe_fp32_peak.restype = ctypes.c_int
+    L.tpcf_probe_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
     L.tpcf_plan_halo.restype = ctypes.c_int
     L.tpcf_plan_halo.argtypes = [_vp, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
     L.tpcf_test_fail_allocation.restype = None

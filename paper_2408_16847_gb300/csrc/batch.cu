@@ -1,11 +1,12 @@
 // Batched execution of several map plans, recorded once into a CUDA graph.
 //
 // A batch runs the estimator of Sec. 3 for n independent maps (any mix of nside,
-// bins and m_max) with a fixed, short launch sequence whose length does not grow
-// with n: the small per-entry kernels take the plan as blockIdx.y, and the
-// persistent pair kernels of all plans that share (m_max, self-pair mode) pull
-// tiles from one concatenated work queue.  The sequence is captured into a graph
-// at creation; every launch replays it.
+// bins, m_max and self-pair mode) with a fixed, short launch sequence whose length
+// does not grow with n: the small per-entry kernels take the plan as blockIdx.y, and
+// one persistent forward and one persistent adjoint launch, compiled for the batch's
+// largest m_max, pull the tiles of every plan from one concatenated work queue (each
+// plan's tiles run with its own m_max, bins and self-pair mode).  The sequence is
+// captured into a graph at creation; every launch replays it.
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -22,14 +23,12 @@ using namespace tpcf;
 
 namespace tpcf {
 #define TPCF_DECL_BATCH_M(m)                                                                                  \
-    cudaError_t batch_fwd_launch_m##m(const BatchItem*, int, long long, unsigned long long*, int, size_t, int, \
+    cudaError_t batch_fwd_launch_m##m(const BatchItem*, int, long long, unsigned long long*, size_t, int,      \
                                       cudaStream_t);                                                          \
     cudaError_t batch_bwd_launch_m##m(const BatchItem*, int, long long, unsigned long long*, size_t, int,      \
                                       cudaStream_t);                                                          \
-    int batch_fwd_occupancy_m##m(size_t, int);                                                                \
-    int batch_bwd_occupancy_m##m(size_t);                                                                     \
-    size_t map_fwd_smem_m##m(int);                                                                            \
-    size_t map_bwd_smem_m##m(int);
+    int batch_fwd_occupancy_m##m(size_t);                                                                     \
+    int batch_bwd_occupancy_m##m(size_t);
 TPCF_DECL_BATCH_M(0) TPCF_DECL_BATCH_M(1) TPCF_DECL_BATCH_M(2) TPCF_DECL_BATCH_M(3) TPCF_DECL_BATCH_M(4)
 TPCF_DECL_BATCH_M(5) TPCF_DECL_BATCH_M(6) TPCF_DECL_BATCH_M(7) TPCF_DECL_BATCH_M(8) TPCF_DECL_BATCH_M(9)
 TPCF_DECL_BATCH_M(10) TPCF_DECL_BATCH_M(11) TPCF_DECL_BATCH_M(12) TPCF_DECL_BATCH_M(13) TPCF_DECL_BATCH_M(14)
@@ -37,16 +36,12 @@ TPCF_DECL_BATCH_M(15) TPCF_DECL_BATCH_M(16)
 #undef TPCF_DECL_BATCH_M
 
 struct BLaunch {
-    cudaError_t (*fwd)(const BatchItem*, int, long long, unsigned long long*, int, size_t, int, cudaStream_t);
+    cudaError_t (*fwd)(const BatchItem*, int, long long, unsigned long long*, size_t, int, cudaStream_t);
     cudaError_t (*bwd)(const BatchItem*, int, long long, unsigned long long*, size_t, int, cudaStream_t);
-    int (*fwd_occ)(size_t, int);
+    int (*fwd_occ)(size_t);
     int (*bwd_occ)(size_t);
-    size_t (*fwd_smem)(int);
-    size_t (*bwd_smem)(int);
 };
-#define TPCF_BROW(m)                                                                                    \
-    {batch_fwd_launch_m##m, batch_bwd_launch_m##m, batch_fwd_occupancy_m##m, batch_bwd_occupancy_m##m, \
-     map_fwd_smem_m##m, map_bwd_smem_m##m}
+#define TPCF_BROW(m) {batch_fwd_launch_m##m, batch_bwd_launch_m##m, batch_fwd_occupancy_m##m, batch_bwd_occupancy_m##m}
 static const BLaunch kBatch[TPCF_MAX_M + 1] = {
     TPCF_BROW(0),  TPCF_BROW(1),  TPCF_BROW(2),  TPCF_BROW(3),  TPCF_BROW(4),  TPCF_BROW(5),
     TPCF_BROW(6),  TPCF_BROW(7),  TPCF_BROW(8),  TPCF_BROW(9),  TPCF_BROW(10), TPCF_BROW(11),
@@ -55,9 +50,10 @@ static const BLaunch kBatch[TPCF_MAX_M + 1] = {
 }  // namespace tpcf
 
 namespace {
-// Plans of one batch that share (m_max, self-pair mode): one pair-kernel launch each way.
+// The plans of a batch: one pair-kernel launch each way, compiled for their largest
+// m_max.
 struct Group {
-    int M = 0, self = 0;
+    int M = 0;
     std::vector<int> members;  // indices into the batch's plan list
     BatchItem* d_items = nullptr;
     long long total_tiles = 0;
@@ -109,7 +105,7 @@ static tpcf_status record(tpcf_batch_s* B, int num_sms, int max_nent, int max_no
     TRY_CUDA(cudaMemsetAsync(B->d_counters, 0, sizeof(unsigned long long) * 2 * B->groups.size(), s));
     for (size_t gi = 0; gi < B->groups.size(); ++gi) {
         const Group& G = B->groups[gi];
-        TRY_CUDA(kBatch[G.M].fwd(G.d_items, (int)G.members.size(), G.total_tiles, B->d_counters + 2 * gi, G.self,
+        TRY_CUDA(kBatch[G.M].fwd(G.d_items, (int)G.members.size(), G.total_tiles, B->d_counters + 2 * gi,
                                  G.fwd_smem, G.fwd_grid, s));
         B->kernels += 1;
     }
@@ -138,19 +134,11 @@ static tpcf_status batch_build(tpcf_batch_s* B, const tpcf_plan* plans, const fl
     TRY_CUDA(cudaGetDevice(&dev));
     TRY_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
 
-    // groups keyed by (m_max, self-pair mode), in order of first appearance
-    std::map<std::pair<int, int>, int> key;
+    // one group: every plan, compiled for the largest m_max
+    B->groups.emplace_back();
     for (int i = 0; i < n; ++i) {
-        const tpcf_plan P = plans[i];
-        const int self = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
-        auto it = key.find({P->M, self});
-        if (it == key.end()) {
-            it = key.emplace(std::make_pair(P->M, self), (int)B->groups.size()).first;
-            B->groups.emplace_back();
-            B->groups.back().M = P->M;
-            B->groups.back().self = self;
-        }
-        B->groups[it->second].members.push_back(i);
+        B->groups[0].members.push_back(i);
+        B->groups[0].M = std::max(B->groups[0].M, plans[i]->M);
     }
 
     // per-plan slots sized for its group's forward grid
@@ -159,10 +147,10 @@ static tpcf_status batch_build(tpcf_batch_s* B, const tpcf_plan* plans, const fl
     for (Group& G : B->groups) {
         for (int i : G.members) {
             const tpcf_plan P = plans[i];
-            G.fwd_smem = std::max(G.fwd_smem, kBatch[G.M].fwd_smem(P->K));
-            G.bwd_smem = std::max(G.bwd_smem, kBatch[G.M].bwd_smem(P->K));
+            G.fwd_smem = std::max(G.fwd_smem, tile_floats_rt(P->K, P->M) * sizeof(float));
+            G.bwd_smem = std::max(G.bwd_smem, bwd_tile_floats_rt(P->K, P->M) * sizeof(float));
         }
-        const int of = kBatch[G.M].fwd_occ(G.fwd_smem, G.self);
+        const int of = kBatch[G.M].fwd_occ(G.fwd_smem);
         TRY_CUDA(cudaGetLastError());
         if (of < 1) {
             set_error("batch forward kernel does not fit on an SM");

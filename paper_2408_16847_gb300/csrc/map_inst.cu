@@ -119,22 +119,14 @@ cudaError_t TPCF_CAT(map_fwd_direct_launch_m, TPCF_M)(const MapDev& g, const Map
 size_t TPCF_CAT(map_fwd_smem_m, TPCF_M)(int K) { return tile_floats<TPCF_M>(K) * sizeof(float); }
 size_t TPCF_CAT(map_bwd_smem_m, TPCF_M)(int K) { return bwd_tile_floats<TPCF_M>(K) * sizeof(float); }
 
-// Batched forward / adjoint over the plans of a batch that share this M (the
-// dynamic shared memory is the largest any of them needs).
+// Batched forward / adjoint over all the plans of a batch whose largest m_max is this
+// M (the dynamic shared memory is the largest any of them needs).
 cudaError_t TPCF_CAT(batch_fwd_launch_m, TPCF_M)(const BatchItem* items, int n, long long total,
-                                                 unsigned long long* counter, int self_subtract, size_t smem,
-                                                 int grid, cudaStream_t s) {
-    if (self_subtract) {
-        auto* k = batch_fwd_kernel<TPCF_M, true>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
-    } else {
-        auto* k = batch_fwd_kernel<TPCF_M, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
-    }
+                                                 unsigned long long* counter, size_t smem, int grid, cudaStream_t s) {
+    auto* k = batch_fwd_kernel<TPCF_M>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
     return cudaGetLastError();
 }
 
@@ -148,25 +140,9 @@ cudaError_t TPCF_CAT(batch_bwd_launch_m, TPCF_M)(const BatchItem* items, int n, 
     return cudaGetLastError();
 }
 
-int TPCF_CAT(batch_fwd_occupancy_m, TPCF_M)(size_t smem, int self_subtract) {
-    int nb = 0;
-    if (self_subtract) {
-        cudaFuncSetAttribute(batch_fwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fwd_kernel<TPCF_M, true>, NTHREADS, smem);
-    } else {
-        cudaFuncSetAttribute(batch_fwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fwd_kernel<TPCF_M, false>, NTHREADS, smem);
-    }
-    return nb;
-}
+int TPCF_CAT(batch_fwd_occupancy_m, TPCF_M)(size_t smem) { return occupancy(batch_fwd_kernel<TPCF_M>, smem); }
 
-int TPCF_CAT(batch_bwd_occupancy_m, TPCF_M)(size_t smem) {
-    int nb = 0;
-    cudaFuncSetAttribute(batch_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_bwd_kernel<TPCF_M>, NTHREADS, smem);
-    return nb;
-}
+int TPCF_CAT(batch_bwd_occupancy_m, TPCF_M)(size_t smem) { return occupancy(batch_bwd_kernel<TPCF_M>, smem); }
 
 // Catalogue forward.
 cudaError_t TPCF_CAT(cat_fwd_launch_m, TPCF_M)(const CatDev& g, const MapCall& c, int grid, cudaStream_t s) {

@@ -199,10 +199,12 @@ __device__ __forceinline__ Fold fold_angle(float cph, float sph) {
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // acc[m] += (wc cos(m phi), ws sin(m phi)), m = 0..M, from the folded angle.
+// mr <= M: the multipoles computed (a runtime m_max below the compiled one).
 template <int M>
-__device__ __forceinline__ void harmonicsf(float2 (&acc)[M + 1], const Fold& f, float wc, float ws) {
+__device__ __forceinline__ void harmonicsf(float2 (&acc)[M + 1], const Fold& f, float wc, float ws, int mr = M) {
     acc[0].x += wc;
     if constexpr (M >= 1) {
+        if (mr < 1) return;
         float2 X = make_float2(wc * f.ac, ws * f.ss);           // X_1 (psi frame)
         float2 D = make_float2(0.5f * f.lam * wc, ws * f.ss);   // X_1 - X_0
         const float2 S2 = make_float2(f.sg, f.sg);
@@ -210,6 +212,7 @@ __device__ __forceinline__ void harmonicsf(float2 (&acc)[M + 1], const Fold& f, 
         acc[1] = __ffma2_rn(S2, X, acc[1]);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
+            if (m > mr) break;
             D = __ffma2_rn(L2, X, D);
             X = __fadd2_rn(X, D);
             acc[m] = (m & 1) ? __ffma2_rn(S2, X, acc[m]) : __fadd2_rn(acc[m], X);
@@ -218,17 +221,19 @@ __device__ __forceinline__ void harmonicsf(float2 (&acc)[M + 1], const Fold& f, 
 }
 
 template <int M>
-__device__ __forceinline__ void harmonics(float2 (&acc)[M + 1], float cph, float sph, float wc, float ws) {
-    harmonicsf<M>(acc, fold_angle(cph, sph), wc, ws);
+__device__ __forceinline__ void harmonics(float2 (&acc)[M + 1], float cph, float sph, float wc, float ws,
+                                          int mr = M) {
+    harmonicsf<M>(acc, fold_angle(cph, sph), wc, ws, mr);
 }
 
 // The same for two pixels a and b at once (two independent chains for
 // instruction-level parallelism), from their folded angles.
 template <int M>
 __device__ __forceinline__ void harmonics2f(float2 (&acc)[M + 1], const Fold& fa, float wca, float wsa,
-                                            const Fold& fb, float wcb, float wsb) {
+                                            const Fold& fb, float wcb, float wsb, int mr = M) {
     acc[0].x += wca + wcb;
     if constexpr (M >= 1) {
+        if (mr < 1) return;
         float2 Xa = make_float2(wca * fa.ac, wsa * fa.ss), Da = make_float2(0.5f * fa.lam * wca, wsa * fa.ss);
         float2 Xb = make_float2(wcb * fb.ac, wsb * fb.ss), Db = make_float2(0.5f * fb.lam * wcb, wsb * fb.ss);
         const float2 Sa = make_float2(fa.sg, fa.sg), Sb = make_float2(fb.sg, fb.sg);
@@ -236,6 +241,7 @@ __device__ __forceinline__ void harmonics2f(float2 (&acc)[M + 1], const Fold& fa
         acc[1] = __ffma2_rn(Sb, Xb, __ffma2_rn(Sa, Xa, acc[1]));
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
+            if (m > mr) break;
             Da = __ffma2_rn(La, Xa, Da);
             Db = __ffma2_rn(Lb, Xb, Db);
             Xa = __fadd2_rn(Xa, Da);
@@ -250,8 +256,8 @@ __device__ __forceinline__ void harmonics2f(float2 (&acc)[M + 1], const Fold& fa
 
 template <int M>
 __device__ __forceinline__ void harmonics2(float2 (&acc)[M + 1], float ca, float sa, float wca, float wsa, float cb,
-                                           float sb, float wcb, float wsb) {
-    harmonics2f<M>(acc, fold_angle(ca, sa), wca, wsa, fold_angle(cb, sb), wcb, wsb);
+                                           float sb, float wcb, float wsb, int mr = M) {
+    harmonics2f<M>(acc, fold_angle(ca, sa), wca, wsa, fold_angle(cb, sb), wcb, wsb, mr);
 }
 
 // A folded angle held by lane `src`, broadcast to the warp.
@@ -305,7 +311,7 @@ struct DirectLoad {
 // wrapping runs) take the general loop.
 template <int M, bool FAST, bool SELF, class L>
 __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
-                                         float2 (&acc)[M + 1], float& W, float& Q, float& QW) {
+                                         float2 (&acc)[M + 1], float& W, float& Q, float& QW, int mr = M) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     if (maxlen <= 0) return;
     const float i0 = (float)(a - c.cint);
@@ -321,7 +327,7 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
             float ca, sa, cb, sb;
             pixel_dir<FAST>(ft, xneg, uneg, R, ca, sa);
             pixel_dir<FAST>(ft + 1.0f, xneg, uneg, R, cb, sb);
-            harmonics2<M>(acc, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x);
+            harmonics2<M>(acc, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x, mr);
             W += v0.y + v1.y;
             if (SELF) {
                 Q = fmaf(v0.x, v0.x, fmaf(v1.x, v1.x, Q));
@@ -341,7 +347,7 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
         float ca, sa, cb, sb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        harmonics2<M>(acc, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x);
+        harmonics2<M>(acc, ca, sa, v0.x, v0.x, cb, sb, v1.x, v1.x, mr);
         W += v0.y + v1.y;
         if (SELF) {
             Q = fmaf(v0.x, v0.x, fmaf(v1.x, v1.x, Q));
@@ -357,7 +363,7 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
 template <int M, bool FAST, bool SELF, class L>
 __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
                                            int mb, float2 (&acc)[M + 1], float& W, float& Q,
-                                           float& QW) {
+                                           float& QW, int mr = M) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     if (maxlen <= 0) return;
     const float i0 = (float)(a - c.cint);
@@ -375,7 +381,7 @@ __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const 
             float ca, sa, cb, sb;
             pixel_dir<FAST>(ft, xneg, uneg, R, ca, sa);
             pixel_dir<FAST>(ft + 1.0f, xneg, uneg, R, cb, sb);
-            harmonics2<M>(acc, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x);
+            harmonics2<M>(acc, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x, mr);
             W += (p0.y + m0.y) + (p1.y + m1.y);
             if (SELF) {
                 Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, fmaf(p1.x, p1.x, fmaf(m1.x, m1.x, Q))));
@@ -400,7 +406,7 @@ __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const 
         float ca, sa, cb, sb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        harmonics2<M>(acc, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x);
+        harmonics2<M>(acc, ca, sa, p0.x + m0.x, p0.x - m0.x, cb, sb, p1.x + m1.x, p1.x - m1.x, mr);
         W += (p0.y + m0.y) + (p1.y + m1.y);
         if (SELF) {
             Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, fmaf(p1.x, p1.x, fmaf(m1.x, m1.x, Q))));
@@ -421,7 +427,8 @@ __device__ __forceinline__ void walk_pairs(const RingCtx& R, const L& ld, const 
 // loads of a step stay coalesced.
 template <int M, bool SELF, class L>
 __device__ __forceinline__ void walk_pairs_shared(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
-                                                  int mb, float2 (&acc)[M + 1], float& W, float& Q, float& QW) {
+                                                  int mb, float2 (&acc)[M + 1], float& W, float& Q, float& QW,
+                                                  int mr = M) {
     if (len <= 0) return;
     const int lane = threadIdx.x & 31;
     const float i0 = (float)(a - c.cint);
@@ -448,7 +455,7 @@ __device__ __forceinline__ void walk_pairs_shared(const RingCtx& R, const L& ld,
             const int ip1 = ip + 1 >= R.n ? ip + 1 - R.n : ip + 1;
             const int im1 = im_ - 1 < 0 ? im_ - 1 + R.n : im_ - 1;
             const float2 p0 = row(ip), m0 = row(im_), p1 = row(ip1), m1 = row(im1);
-            harmonics2f<M>(acc, fa, p0.x + m0.x, p0.x - m0.x, fb, p1.x + m1.x, p1.x - m1.x);
+            harmonics2f<M>(acc, fa, p0.x + m0.x, p0.x - m0.x, fb, p1.x + m1.x, p1.x - m1.x, mr);
             W += (p0.y + m0.y) + (p1.y + m1.y);
             if (SELF) {
                 Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, fmaf(p1.x, p1.x, fmaf(m1.x, m1.x, Q))));
@@ -460,7 +467,7 @@ __device__ __forceinline__ void walk_pairs_shared(const RingCtx& R, const L& ld,
         if (tt < nstep) {
             const Fold fa = shfl_fold(mine, tt);
             const float2 p0 = row(ip), m0 = row(im_);
-            harmonicsf<M>(acc, fa, p0.x + m0.x, p0.x - m0.x);
+            harmonicsf<M>(acc, fa, p0.x + m0.x, p0.x - m0.x, mr);
             W += p0.y + m0.y;
             if (SELF) {
                 Q = fmaf(p0.x, p0.x, fmaf(m0.x, m0.x, Q));
@@ -581,7 +588,7 @@ __device__ __forceinline__ ExactCtx exact_ctx(const MapDev& g, const PivotRing& 
 template <int M, bool SELF, class L>
 __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P, int r, int k, int q,
                                              const L& ld, float2 (&acc)[M + 1], float& W,
-                                             float& Q, float& QW) {
+                                             float& Q, float& QW, int mr = M) {
     const long long pr = P.pair0 + (r - P.rlo);
     const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
     const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
@@ -596,7 +603,7 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
             const float2 v = ld(R.first + wrap_idx(c.cint, R.n));
             float cph, sph;
             pixel_dir<false>(0.0f, 0.0f, -c.cfrac * R.inv_n, R, cph, sph);
-            harmonics<M>(acc, cph, sph, v.x, v.x);
+            harmonics<M>(acc, cph, sph, v.x, v.x, mr);
             W += v.y;
             if (SELF) {
                 Q = fmaf(v.x, v.x, Q);
@@ -604,24 +611,24 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
             }
         }
         if (runs_shared(c, b.a0, b.n0)) {
-            walk_pairs_shared<M, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW);
+            walk_pairs_shared<M, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW, mr);
             return;
         }
         const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
         if (fast)
-            walk_pairs<M, true, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW);
+            walk_pairs<M, true, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW, mr);
         else
-            walk_pairs<M, false, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW);
+            walk_pairs<M, false, SELF>(R, ld, c, b.a0, b.n0, b.mb, acc, W, Q, QW, mr);
         return;
     }
     const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
     const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
     if (fast) {
-        walk_run<M, true, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW);
-        walk_run<M, true, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW);
+        walk_run<M, true, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW, mr);
+        walk_run<M, true, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW, mr);
     } else {
-        walk_run<M, false, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW);
-        walk_run<M, false, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW);
+        walk_run<M, false, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW, mr);
+        walk_run<M, false, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW, mr);
     }
 }
 
@@ -630,7 +637,7 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
 //   W[k][32], Q[k][32], QW[k][32], piv[2][32] (w d, w of the pivots)
 template <int M>
 __host__ __device__ inline size_t tile_floats(int K) {
-    return (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE + 2 * TILE;
+    return tile_floats_rt(K, M);
 }
 
 // Load the tile's pivot description; returns false if no lane has w != 0.
@@ -664,7 +671,7 @@ struct LayKM {
 // Smem must be zeroed beforehand; it is complete after the caller's __syncthreads().
 template <int M, bool SELF, class L, class Lay>
 __device__ __forceinline__ void tile_moments_l(const MapDev& g, const PivotRing& P, int q, const L& ld,
-                                               const Lay& lay, int flush) {
+                                               const Lay& lay, int flush, int mr = M) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < g.K; ++k) {
         const int2 br = g.bin_range[(long long)P.i * g.K + k];
@@ -678,11 +685,12 @@ __device__ __forceinline__ void tile_moments_l(const MapDev& g, const PivotRing&
         // sums short.
         int nr = 0;
         for (int r = br.x + warp; r <= br.y; r += NWARPS) {
-            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, acc, W, Q, QW);
+            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, acc, W, Q, QW, mr);
             if (++nr == flush || r + NWARPS > br.y) {
                 nr = 0;
 #pragma unroll
                 for (int m = 0; m <= M; ++m) {
+                    if (m > mr) break;
                     atomicAdd(lay.a(k, m, 0, lane), acc[m].x);
                     atomicAdd(lay.a(k, m, 1, lane), acc[m].y);
                     acc[m] = make_float2(0.0f, 0.0f);
@@ -702,8 +710,8 @@ __device__ __forceinline__ void tile_moments_l(const MapDev& g, const PivotRing&
 
 template <int M, bool SELF, class L>
 __device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P, int q, const L& ld, float* sA,
-                                             float* sW, float* sQ, float* sQW, int flush) {
-    tile_moments_l<M, SELF>(g, P, q, ld, LayKM{sA, sW, sQ, sQW, M + 1}, flush);
+                                             float* sW, float* sQ, float* sQW, int flush, int mr = M) {
+    tile_moments_l<M, SELF>(g, P, q, ld, LayKM{sA, sW, sQ, sQW, mr + 1}, flush, mr);
 }
 
 // Per-tile partial sums into the CTA's FP64 slot (eq. zetamEst2 summed over the
@@ -712,9 +720,9 @@ __device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P
 template <int M>
 __device__ __forceinline__ void tile_contract(int K, const float* sA, const float* sW, const float* sQ,
                                               const float* sQW, const float* sPiv, double* slot,
-                                              bool self) {
+                                              bool self, int mr = M) {
     const int P = n_pairs_tri(K);
-    const int nS = (M + 1) * P;
+    const int nS = (mr + 1) * P;
     const float* wd = sPiv;
     const float* wt = sPiv + TILE;
     for (int e = threadIdx.x; e < nS + P + (self ? K : 0); e += NTHREADS) {
@@ -725,9 +733,9 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
             while (k2 * (k2 + 1) / 2 > pidx) --k2;
             while ((k2 + 1) * (k2 + 2) / 2 <= pidx) ++k2;
             const int k1 = pidx - k2 * (k2 + 1) / 2;
-            const float* r1 = sA + ((size_t)k1 * (M + 1) + m) * 2 * TILE;
+            const float* r1 = sA + ((size_t)k1 * (mr + 1) + m) * 2 * TILE;
             const float* i1 = r1 + TILE;
-            const float* r2 = sA + ((size_t)k2 * (M + 1) + m) * 2 * TILE;
+            const float* r2 = sA + ((size_t)k2 * (mr + 1) + m) * 2 * TILE;
             const float* i2 = r2 + TILE;
             float sr = 0.0f, si = 0.0f;
             // start each thread at its own lane so a warp's 32 rows hit 32 banks
@@ -774,9 +782,10 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
 // in the convention a = re - i im; D is the Gram matrix of the W^k rows with the
 // weights w.  On the 5th-generation tensor cores (kind::tf32, FP32 accumulation in
 // tensor memory), per block of rows (each m, then the W block):
-//   * the moments are accumulated straight into the layout the MMA reads: rows of 32
-//     pivots (128 B), 16-byte chunks XOR-swizzled by the row index (the 128-byte
-//     swizzle), blocks starting on 1024-byte boundaries; no operand copy of X exists;
+//   * the moments are accumulated straight into the layout the MMA reads (K-major,
+//     no swizzle: 8-row x 16-byte core matrices, pivot-adjacent ones 128 B apart,
+//     8-row groups 1024 B apart, blocks starting on a row group); no operand copy of
+//     X exists;
 //   * with Y = X diag(sqrt|w d|) and s = sign(w d), G = Y diag(s) Y^T.  Y is split into
 //     a tf32 part hi (its low 13 mantissa bits cleared, written back in place) and
 //     the fp32 remainder lo, and G = hi s hi^T + C + C^T with C = hi s lo^T (the
@@ -792,8 +801,8 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
 constexpr int TC_TMEM_COLS = 128;  // two accumulators of up to 64 columns
 constexpr int ST_TC_TIMEOUT = ST_TC_TIMEOUT_BIT;
 
-// Shared-memory plan of the tensor-core forward tile (in floats from a 1024-byte
-// aligned base).
+// Shared-memory plan of the tensor-core forward tile (in floats from the dynamic
+// shared memory base; blocks start on 8-row groups).
 struct TcLayout {
     int Rm, RD, NBm, NBd;  // rows per m block and of the W block; MMA N of each
     int x0, D0;            // first row of the moments; first row of the W block
@@ -825,22 +834,24 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, bool self) {
     return L;
 }
 
-// bytes of dynamic shared memory (1 KB of slack for the 1024-byte alignment)
+// bytes of dynamic shared memory
 __host__ __device__ inline size_t tc_smem_bytes(int K, int M, bool self) {
-    return (size_t)tc_layout(K, M, self).total * sizeof(float) + 1024;
+    return (size_t)tc_layout(K, M, self).total * sizeof(float);
 }
 
-// Position of (row r, pivot p) in a 128-byte-swizzled block of 32-float rows.
-__device__ __forceinline__ int sw128(int r, int p) { return r * TILE + ((((p >> 2) ^ (r & 7)) << 2) | (p & 3)); }
+// Position of (row r, pivot p) in the K-major canonical layout without swizzle: core
+// matrices of 8 rows x 4 pivots (128 contiguous bytes, rows 16 B apart), the 8
+// pivot-adjacent core matrices of a row group 128 B apart, row groups 1024 B apart.
+__device__ __forceinline__ int kmaj(int r, int p) { return ((r >> 3) << 8) + ((p >> 2) << 5) + ((r & 7) << 2) + (p & 3); }
 
-struct LaySW {
+struct LayTC {
     float* sX;
     float *sQ, *sQW;
     int Rm, D0;
     __device__ __forceinline__ float* a(int k, int m, int part, int lane) const {
-        return sX + sw128(m * Rm + 2 * k + part, lane);
+        return sX + kmaj(m * Rm + 2 * k + part, lane);
     }
-    __device__ __forceinline__ float* w(int k, int lane) const { return sX + sw128(D0 + k, lane); }
+    __device__ __forceinline__ float* w(int k, int lane) const { return sX + kmaj(D0 + k, lane); }
     __device__ __forceinline__ float* q(int k, int lane) const { return sQ + k * TILE + lane; }
     __device__ __forceinline__ float* qw(int k, int lane) const { return sQW + k * TILE + lane; }
 };
@@ -849,11 +860,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// UMMA shared-memory descriptor, K-major, 128-byte swizzle: start address, stride
-// between 8-row groups 1024 B, descriptor version 1, layout type 2 (128-byte swizzle).
-__device__ __forceinline__ uint64_t tc_sdesc_sw128(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024u >> 4) << 32) |
-           (1ull << 46) | (2ull << 61);
+// UMMA shared-memory descriptor, K-major without swizzle: start address, leading
+// (pivot-direction) core-matrix offset 128 B, row-group stride 1024 B, descriptor
+// version 1.
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46);
 }
 
 // Instruction descriptor: D f32, A and B tf32, both K-major, N, M = 128.
@@ -967,16 +979,18 @@ __device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, 
         const int r0 = isD ? L.D0 : b * L.Rm;
         float* Blo = Bhi + N * TILE;
         // split the block: hi in place, (s hi, s lo) into the staging rows; rows of B
-        // beyond the block are zero
+        // beyond the block are zero.  e runs over the layout in memory order (row group,
+        // pivot chunk, row in group, pivot in chunk); r0 is a multiple of 8, so the
+        // block's element e sits at sX[r0 * 32 + e] and B's at B[e].
         for (int e = threadIdx.x; e < N * TILE; e += NTHREADS) {
-            const int i = e >> 5, cp = e & 31;
-            const int p = (((cp >> 2) ^ (i & 7)) << 2) | (cp & 3);  // r0 is a multiple of 8
+            const int i = ((e >> 8) << 3) + ((e >> 2) & 7);
+            const int p = (((e >> 5) & 7) << 2) + (e & 3);
             float bh = 0.0f, bl = 0.0f;
             if (i < rows) {
-                const float x = sX[(r0 + i) * TILE + cp] * (isD ? sc[2 * TILE + p] : sc[p]);
+                const float x = sX[r0 * TILE + e] * (isD ? sc[2 * TILE + p] : sc[p]);
                 const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
                 const float sg = isD ? 1.0f : sc[TILE + p];
-                sX[(r0 + i) * TILE + cp] = hi;
+                sX[r0 * TILE + e] = hi;
                 bh = sg * hi;
                 bl = sg * (x - hi);
             }
@@ -991,9 +1005,9 @@ __device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, 
             const uint32_t a0 = smem_u32(sX + r0 * TILE), bh = smem_u32(Bhi), bl = smem_u32(Blo);
 #pragma unroll
             for (int k8 = 0; k8 < TILE / 8; ++k8) {
-                const uint32_t o = (uint32_t)k8 * 32u;  // 8 tf32 pivots per MMA
-                tc_mma(tc.tmem, tc_sdesc_sw128(a0 + o), tc_sdesc_sw128(bh + o), idesc, k8 > 0);
-                tc_mma(tc.tmem + (uint32_t)L.NBm, tc_sdesc_sw128(a0 + o), tc_sdesc_sw128(bl + o), idesc, k8 > 0);
+                const uint32_t o = (uint32_t)k8 * 256u;  // 8 tf32 pivots = two core matrices per MMA
+                tc_mma(tc.tmem, tc_sdesc(a0 + o), tc_sdesc(bh + o), idesc, k8 > 0);
+                tc_mma(tc.tmem + (uint32_t)L.NBm, tc_sdesc(a0 + o), tc_sdesc(bl + o), idesc, k8 > 0);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              tc.mbar)
@@ -1080,15 +1094,16 @@ __device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, 
 // One forward tile: the moments of its 32 pivots, then their partial sums added to
 // the CTA's slot.  Called by every thread of the CTA (contains barriers).
 template <int M, bool SELF, bool DIRECT>
-__device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem) {
+__device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem,
+                                         int mr = M) {
     const int K = g.K;
     float* sA = smem;
-    float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
+    float* sW = sA + (size_t)K * (mr + 1) * 2 * TILE;
     float* sQ = sW + K * TILE;
     float* sQW = sQ + K * TILE;
     float* sPiv = sQW + K * TILE;
     const int lane = threadIdx.x & 31;
-    const size_t nfl = tile_floats<M>(K) - 2 * TILE;
+    const size_t nfl = tile_floats_rt(K, mr) - 2 * TILE;
     const int2 tq = g.tiles[tile];
     if (tq.x < 0 || tq.x >= g.nrings) {
         if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
@@ -1112,16 +1127,16 @@ __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int 
     }
     __syncthreads();
     if (DIRECT)
-        tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW, c.flush);
+        tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW, c.flush, mr);
     else
-        tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush);
+        tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush, mr);
     __syncthreads();
-    tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+    tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF && c.self_subtract, mr);
     __syncthreads();
 }
 
 // One forward tile with the tensor-core contraction: the moments accumulate in the
-// swizzled layout of tc_layout(), then tile_contract_tc.
+// tensor-core layout of tc_layout(), then tile_contract_tc.
 template <int M, bool SELF>
 __device__ __forceinline__ void fwd_tile_tc(const MapDev& g, const MapCall& c, int tile, double* slot, float* base,
                                             TcState& tc) {
@@ -1156,7 +1171,7 @@ __device__ __forceinline__ void fwd_tile_tc(const MapDev& g, const MapCall& c, i
     {
         const int Rm = (2 * K + 7) & ~7, D0 = (M + 1) * Rm;
         const TcLayout L = tc_layout(K, M, SELF);
-        tile_moments_l<M, SELF>(g, P, qg, PackedLoad{c.wdw}, LaySW{base, base + L.offQ, base + L.offQW, Rm, D0},
+        tile_moments_l<M, SELF>(g, P, qg, PackedLoad{c.wdw}, LayTC{base, base + L.offQ, base + L.offQW, Rm, D0},
                                 c.flush);
     }
     __syncthreads();
@@ -1184,7 +1199,7 @@ __global__ void __launch_bounds__(NTHREADS, OCC) map_fwd_kernel(MapDev g, MapCal
 // memory allows it; 128 accumulator columns each, so at most 4 fit an SM's TMEM).
 template <int M, bool SELF>
 __global__ void __launch_bounds__(NTHREADS, 3) map_fwd_tc_kernel(MapDev g, MapCall c) {
-    extern __shared__ __align__(1024) float smem_tc[];
+    extern __shared__ __align__(16) float smem_tc[];
     __shared__ int s_tile;
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
@@ -1192,9 +1207,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) map_fwd_tc_kernel(MapDev g, MapCa
     if (threadIdx.x == 0) s_fail = 0;
     tc_setup(&s_tmem, &s_mbar);
     TcState tc{s_tmem, smem_u32(&s_mbar), 0u, &s_fail};
-    // 1024-byte aligned base of the swizzled blocks
-    const uint32_t mis = smem_u32(smem_tc) & 1023u;
-    float* base = smem_tc + (mis ? (1024u - mis) / 4 : 0u);
+    // the no-swizzle operand layout needs 16-byte alignment only
+    float* base = smem_tc;
     double* slot = c.slots + (size_t)blockIdx.x * n_entries(g.K, M);
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
@@ -1206,10 +1220,12 @@ __global__ void __launch_bounds__(NTHREADS, 3) map_fwd_tc_kernel(MapDev g, MapCa
     tc_teardown(s_tmem);
 }
 
-// Batched forward over the plans of a batch that share M: one work queue over the
+// Batched forward over all the plans of a batch, one launch: one work queue over the
 // concatenated tiles of all its plans (plan-major); each CTA adds into that plan's
-// slot number blockIdx.x.
-template <int M, bool SELF>
+// slot number blockIdx.x.  Compiled for the largest m_max of the batch (M); each
+// plan's tiles run with its own m_max (the multipole loops stop there) and its own
+// shared-memory layout, and with its own self-pair mode.
+template <int M>
 __global__ void __launch_bounds__(NTHREADS, 2) batch_fwd_kernel(const BatchItem* __restrict__ items, int n,
                                                                long long total, unsigned long long* counter) {
     extern __shared__ float smem[];
@@ -1228,8 +1244,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) batch_fwd_kernel(const BatchItem*
             if (s_first[mid] <= t) lo = mid; else hi = mid - 1;
         }
         const BatchItem& it = items[lo];
-        double* slot = it.c.slots + (size_t)blockIdx.x * n_entries(it.g.K, M);
-        fwd_tile<M, SELF, false>(it.g, it.c, (int)(t - s_first[lo]), slot, smem);
+        double* slot = it.c.slots + (size_t)blockIdx.x * n_entries(it.g.K, it.g.M);
+        fwd_tile<M, true, false>(it.g, it.c, (int)(t - s_first[lo]), slot, smem, it.g.M);
     }
 }
 
@@ -1293,18 +1309,23 @@ __global__ void __launch_bounds__(NTHREADS) map_count_kernel(MapDev g, const flo
 // neighbour rings again; each warp gathers its ring's contributions in a shared-memory
 // row buffer and flushes the row to the gradient with one atomic add per pixel.
 
-constexpr int ROW = 512;  // floats per warp row buffer (wider rows fall back to whole-ring or global adds)
 
 // val = sum_m (cos(m phi) hr_m + sin(m phi) hi_m): X the cosine part, Y the sine part.
 // h[m] = (hr_m, hi_m); the (cos, sin) chains run packed, in the folded frame psi, by
 // the recurrence of harmonics(); even and odd multipoles are summed apart and the odd
 // sum takes the sign sigma at the end.
 template <int M>
-__device__ __forceinline__ void adj_harmonicsf(const float2 (&h)[M + 1], const Fold& f, float& X, float& Y) {
+__device__ __forceinline__ void adj_harmonicsf(const float2 (&h)[M + 1], const Fold& f, float& X, float& Y,
+                                               int mr = M) {
     float2 ev = make_float2(h[0].x, 0.0f);
     float2 od = make_float2(0.0f, 0.0f);
     float sg = 1.0f;
     if constexpr (M >= 1) {
+        if (mr < 1) {
+            X = ev.x;
+            Y = ev.y;
+            return;
+        }
         sg = f.sg;
         float2 T = make_float2(f.ac, f.ss);
         float2 D = make_float2(0.5f * f.lam, f.ss);
@@ -1312,6 +1333,7 @@ __device__ __forceinline__ void adj_harmonicsf(const float2 (&h)[M + 1], const F
         od = __ffma2_rn(T, h[1], od);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
+            if (m > mr) break;
             D = __ffma2_rn(L2, T, D);
             T = __fadd2_rn(T, D);
             if (m & 1)
@@ -1325,8 +1347,9 @@ __device__ __forceinline__ void adj_harmonicsf(const float2 (&h)[M + 1], const F
 }
 
 template <int M>
-__device__ __forceinline__ void adj_harmonics(const float2 (&h)[M + 1], float cph, float sph, float& X, float& Y) {
-    adj_harmonicsf<M>(h, fold_angle(cph, sph), X, Y);
+__device__ __forceinline__ void adj_harmonics(const float2 (&h)[M + 1], float cph, float sph, float& X, float& Y,
+                                              int mr = M) {
+    adj_harmonicsf<M>(h, fold_angle(cph, sph), X, Y, mr);
 }
 
 // Where the contribution to pixel p (unwrapped index on ring R) goes.
@@ -1348,11 +1371,16 @@ __device__ __forceinline__ void sink_add(const RowSink& s, int p_unwrapped, int 
 
 template <int M>
 __device__ __forceinline__ void adj_harmonics2f(const float2 (&h)[M + 1], const Fold& fa, const Fold& fb, float& Xa,
-                                                float& Ya, float& Xb, float& Yb) {
+                                                float& Ya, float& Xb, float& Yb, int mr = M) {
     float2 eva = make_float2(h[0].x, 0.0f), evb = eva;
     float2 oda = make_float2(0.0f, 0.0f), odb = oda;
     float sga = 1.0f, sgb = 1.0f;
     if constexpr (M >= 1) {
+        if (mr < 1) {
+            Xa = Xb = eva.x;
+            Ya = Yb = eva.y;
+            return;
+        }
         sga = fa.sg;
         sgb = fb.sg;
         float2 Ta = make_float2(fa.ac, fa.ss), Da = make_float2(0.5f * fa.lam, fa.ss);
@@ -1362,6 +1390,7 @@ __device__ __forceinline__ void adj_harmonics2f(const float2 (&h)[M + 1], const 
         odb = __ffma2_rn(Tb, h[1], odb);
 #pragma unroll
         for (int m = 2; m <= M; ++m) {
+            if (m > mr) break;
             Da = __ffma2_rn(La, Ta, Da);
             Db = __ffma2_rn(Lb, Tb, Db);
             Ta = __fadd2_rn(Ta, Da);
@@ -1383,14 +1412,14 @@ __device__ __forceinline__ void adj_harmonics2f(const float2 (&h)[M + 1], const 
 
 template <int M>
 __device__ __forceinline__ void adj_harmonics2(const float2 (&h)[M + 1], float ca, float sa, float cb, float sb,
-                                               float& Xa, float& Ya, float& Xb, float& Yb) {
-    adj_harmonics2f<M>(h, fold_angle(ca, sa), fold_angle(cb, sb), Xa, Ya, Xb, Yb);
+                                               float& Xa, float& Ya, float& Xb, float& Yb, int mr = M) {
+    adj_harmonics2f<M>(h, fold_angle(ca, sa), fold_angle(cb, sb), Xa, Ya, Xb, Yb, mr);
 }
 
 template <int M, bool FAST, bool SELF = false>
 __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
                                         int a, int len, const float2 (&h)[M + 1], float wdi, const RowSink& s,
-                                        float ck = 0.0f) {
+                                        float ck = 0.0f, int mr = M) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
@@ -1406,7 +1435,7 @@ __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restri
         float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
+        adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb, mr);
         if (SELF) {  // self-pair subtraction: -2 cdiag_k (w_p d_p) per neighbour p
             Xa = fmaf(ck, v0.x, Xa);
             Xb = fmaf(ck, v1.x, Xb);
@@ -1420,7 +1449,7 @@ __device__ __forceinline__ void adj_run(const RingCtx& R, const float2* __restri
 template <int M, bool FAST, bool SELF = false>
 __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
                                           int a, int len, int mb, const float2 (&h)[M + 1], float wdi,
-                                          const RowSink& s, float ck = 0.0f) {
+                                          const RowSink& s, float ck = 0.0f, int mr = M) {
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     const float i0 = (float)(a - c.cint);
     const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
@@ -1440,7 +1469,7 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
         float ca, sa, cb, sb, Xa, Ya, Xb, Yb;
         pixel_dir<FAST>(oa, xneg, uneg, R, ca, sa);
         pixel_dir<FAST>(ob, xneg, uneg, R, cb, sb);
-        adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb);
+        adj_harmonics2<M>(h, ca, sa, cb, sb, Xa, Ya, Xb, Yb, mr);
         if (on0) {
             sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya + (SELF ? ck * p0.x : 0.0f)));
             sink_add(s, mb - a - t, im_, wdi * m0.y * (Xa - Ya + (SELF ? ck * m0.x : 0.0f)));
@@ -1459,7 +1488,7 @@ __device__ __forceinline__ void adj_pairs(const RingCtx& R, const float2* __rest
 template <int M, bool SELF = false>
 __device__ __forceinline__ void adj_pairs_shared(const RingCtx& R, const float2* __restrict__ wdw, const LaneC& c,
                                                  int a, int len, int mb, const float2 (&h)[M + 1], float wdi,
-                                                 const RowSink& s, float ck = 0.0f) {
+                                                 const RowSink& s, float ck = 0.0f, int mr = M) {
     if (len <= 0) return;
     const int lane = threadIdx.x & 31;
     const float i0 = (float)(a - c.cint);
@@ -1489,7 +1518,7 @@ __device__ __forceinline__ void adj_pairs_shared(const RingCtx& R, const float2*
             const float2 p1 = two ? __ldg(row + ip1) : make_float2(0.0f, 0.0f);
             const float2 m1 = two ? __ldg(row + im1) : make_float2(0.0f, 0.0f);
             float Xa, Ya, Xb, Yb;
-            adj_harmonics2f<M>(h, fa, fb, Xa, Ya, Xb, Yb);
+            adj_harmonics2f<M>(h, fa, fb, Xa, Ya, Xb, Yb, mr);
             sink_add(s, a + t, ip, wdi * p0.y * (Xa + Ya + (SELF ? ck * p0.x : 0.0f)));
             sink_add(s, mb - a - t, im_, wdi * m0.y * (Xa - Ya + (SELF ? ck * m0.x : 0.0f)));
             if (two) {
@@ -1507,7 +1536,7 @@ template <int M, bool SELF = false>
 __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, int r, int q, float wdi,
                                          const float2* __restrict__ wdw, const float* sH, float* rowbuf,
                                          float* grad, int* status,
-                                         const float* cdiag = nullptr) {
+                                         const float* cdiag = nullptr, int mr = M) {
     const int lane = threadIdx.x & 31;
     const long long pr = P.pair0 + (r - P.rlo);
     const int2 TK = g.pair_T[pr * (g.K + 1) + g.K];
@@ -1552,10 +1581,11 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
         const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
         if (Tk.x == T_INF || Tk1.x == T_ZERO) continue;
         float2 h[M + 1];
-        const float* hk = sH + (size_t)k * (M + 1) * 2 * TILE;
+        const float* hk = sH + (size_t)k * (mr + 1) * 2 * TILE;
 #pragma unroll
         for (int m = 0; m <= M; ++m) {
-            h[m] = make_float2(hk[(2 * m) * TILE + lane], hk[(2 * m + 1) * TILE + lane]);
+            h[m] = m <= mr ? make_float2(hk[(2 * m) * TILE + lane], hk[(2 * m + 1) * TILE + lane])
+                           : make_float2(0.0f, 0.0f);
         }
         const bool sym = (R.n == P.n_i) && (Tk1.x != T_INF);
         const BinRuns b = bin_runs(c, Tk, Tk1, g.E[k], g.E[k + 1], x, R.n, sym);
@@ -1567,28 +1597,28 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
                 const float2 v = __ldg(wdw + R.first + pw);
                 float cph, sph, X, Y;
                 pixel_dir<false>(0.0f, 0.0f, -c.cfrac * R.inv_n, R, cph, sph);
-                adj_harmonics<M>(h, cph, sph, X, Y);
+                adj_harmonics<M>(h, cph, sph, X, Y, mr);
                 if (SELF) X = fmaf(ck, v.x, X);
                 sink_add(s, p, pw, wdi * v.y * (X + Y));
             }
             if (runs_shared(c, b.a0, b.n0)) {
-                adj_pairs_shared<M, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
+                adj_pairs_shared<M, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck, mr);
             } else {
                 const bool fast = __all_sync(0xffffffffu, run_omax(c, b.a0, b.n0) * R.step <= FAST_XMAX);
                 if (fast)
-                    adj_pairs<M, true, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
+                    adj_pairs<M, true, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck, mr);
                 else
-                    adj_pairs<M, false, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck);
+                    adj_pairs<M, false, SELF>(R, wdw, c, b.a0, b.n0, b.mb, h, wdi, s, ck, mr);
             }
         } else {
             const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
             const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
             if (fast) {
-                adj_run<M, true, SELF>(R, wdw, c, b.a0, b.n0, h, wdi, s, ck);
-                adj_run<M, true, SELF>(R, wdw, c, b.a1, b.n1, h, wdi, s, ck);
+                adj_run<M, true, SELF>(R, wdw, c, b.a0, b.n0, h, wdi, s, ck, mr);
+                adj_run<M, true, SELF>(R, wdw, c, b.a1, b.n1, h, wdi, s, ck, mr);
             } else {
-                adj_run<M, false, SELF>(R, wdw, c, b.a0, b.n0, h, wdi, s, ck);
-                adj_run<M, false, SELF>(R, wdw, c, b.a1, b.n1, h, wdi, s, ck);
+                adj_run<M, false, SELF>(R, wdw, c, b.a0, b.n0, h, wdi, s, ck, mr);
+                adj_run<M, false, SELF>(R, wdw, c, b.a1, b.n1, h, wdi, s, ck, mr);
             }
         }
     }
@@ -1610,10 +1640,7 @@ __device__ __forceinline__ void adj_ring(const MapDev& g, const PivotRing& P, in
 // and puts the warps' row buffers where W and the rest were.
 template <int M>
 __host__ __device__ inline size_t bwd_tile_floats(int K) {
-    const size_t a = (size_t)K * (M + 1) * 2 * TILE;
-    const size_t p12 = a + 3 * (size_t)K * TILE + 2 * TILE + TILE + (size_t)K * K * 2;
-    const size_t p3 = a + (size_t)NWARPS * ROW;
-    return p12 > p3 ? p12 : p3;
+    return bwd_tile_floats_rt(K, M);
 }
 
 // One adjoint tile (all three phases).  Called by every thread of the CTA.  With
@@ -1621,10 +1648,10 @@ __host__ __device__ inline size_t bwd_tile_floats(int K) {
 // cdiag_k = sum_m Re C_m(k,k), -w_p Q^k(p) cdiag_k to a pivot and
 // -2 w_p^2 d_p w_i d_i cdiag_k to each neighbour p of pivot i.
 template <int M, bool SELF = false>
-__device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int tile, float* smem) {
+__device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int tile, float* smem, int mr = M) {
     const int K = g.K;
     float* sA = smem;
-    float* sW = sA + (size_t)K * (M + 1) * 2 * TILE;
+    float* sW = sA + (size_t)K * (mr + 1) * 2 * TILE;
     float* sQ = sW + K * TILE;
     float* sQW = sQ + K * TILE;
     float* sPiv = sQW + K * TILE;
@@ -1632,7 +1659,7 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
     float* sHm = sPrim + TILE;                  // [K][K][2] one m at a time
     float* sRow = sW;                           // [NWARPS][ROW], phase 3 only
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t nfl = (size_t)K * (M + 1) * 2 * TILE + 3 * (size_t)K * TILE;
+    const size_t nfl = (size_t)K * (mr + 1) * 2 * TILE + 3 * (size_t)K * TILE;
 
     const int2 tq = g.tiles[tile];
     if (tq.x < 0 || tq.x >= g.nrings) {
@@ -1655,10 +1682,10 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
     }
     __syncthreads();
     // phase 1: the tile's moments, exactly as in the forward
-    tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush);
+    tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush, mr);
     __syncthreads();
     // phase 2: h = H conj(a) per m, in place; primary term (1/2) sum Re[a h]
-    for (int m = 0; m <= M; ++m) {
+    for (int m = 0; m <= mr; ++m) {
         for (int e = threadIdx.x; e < K * K * 2; e += NTHREADS)
             sHm[e] = c.H[(size_t)m * K * K * 2 + e];
         __syncthreads();
@@ -1670,12 +1697,12 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
             float hr = 0.0f, hi = 0.0f;
             for (int kp = 0; kp < K; ++kp) {
                 const float Hr = sHm[(k * K + kp) * 2], Hi = sHm[(k * K + kp) * 2 + 1];
-                const float* ap = sA + ((size_t)kp * (M + 1) + m) * 2 * TILE;
+                const float* ap = sA + ((size_t)kp * (mr + 1) + m) * 2 * TILE;
                 const float tr = ap[l], ti = ap[TILE + l];
                 hr = fmaf(Hr, tr, fmaf(-Hi, ti, hr));
                 hi = fmaf(Hr, ti, fmaf(Hi, tr, hi));
             }
-            const float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+            const float* ak = sA + ((size_t)k * (mr + 1) + m) * 2 * TILE;
             atomicAdd(sPrim + l, fmaf(ak[l], hr, ak[TILE + l] * hi));
             hrv[nmine] = hr;
             hiv[nmine] = hi;
@@ -1684,13 +1711,13 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
         nmine = 0;
         for (int e = threadIdx.x; e < K * TILE; e += NTHREADS, ++nmine) {
             const int k = e / TILE, l = e - k * TILE;
-            float* ak = sA + ((size_t)k * (M + 1) + m) * 2 * TILE;
+            float* ak = sA + ((size_t)k * (mr + 1) + m) * 2 * TILE;
             ak[l] = hrv[nmine];
             ak[TILE + l] = hiv[nmine];
         }
         __syncthreads();
     }
-    const float* cdiag = SELF ? c.H + (size_t)(M + 1) * K * K * 2 : nullptr;
+    const float* cdiag = SELF ? c.H + (size_t)(mr + 1) * K * K * 2 : nullptr;
     if (threadIdx.x < TILE && in) {
         float gp = 0.5f * pv.y * sPrim[lane];
         if (SELF) {
@@ -1704,7 +1731,7 @@ __device__ __forceinline__ void bwd_tile(const MapDev& g, const MapCall& c, int 
     // phase 3: neighbour legs, warps split the neighbour rings
     const int2 rr = g.ring_range[P.i];
     for (int r = rr.x + warp; r <= rr.y; r += NWARPS)
-        adj_ring<M, SELF>(g, P, r, qg, pv.x, c.wdw, sA, sRow + (size_t)warp * ROW, c.grad, c.status, cdiag);
+        adj_ring<M, SELF>(g, P, r, qg, pv.x, c.wdw, sA, sRow + (size_t)warp * ROW, c.grad, c.status, cdiag, mr);
     __syncthreads();
 }
 
@@ -1739,7 +1766,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) batch_bwd_kernel(const BatchItem*
             const int mid = (lo + hi + 1) / 2;
             if (s_first[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        bwd_tile<M>(items[lo].g, items[lo].c, (int)(t - s_first[lo]), smem);
+        bwd_tile<M>(items[lo].g, items[lo].c, (int)(t - s_first[lo]), smem, items[lo].g.M);
     }
 }
 

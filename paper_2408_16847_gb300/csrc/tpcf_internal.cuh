@@ -99,6 +99,24 @@ inline __host__ __device__ int n_entries(int K, int M) {
     return 2 * (M + 1) * n_pairs_tri(K) + n_pairs_tri(K) + 2 * K;
 }
 
+constexpr int ROW = 512;  // floats per warp row buffer of the adjoint (wider rows: whole-ring or global adds)
+
+// Shared memory (floats) of a map forward tile with runtime m_max mr: moments
+// A[k][m][re/im][32], W, Q, QW [k][32], the pivots' (w d, w).
+__host__ __device__ inline size_t tile_floats_rt(int K, int mr) {
+    return (size_t)K * (mr + 1) * 2 * TILE + 3 * (size_t)K * TILE + 2 * TILE;
+}
+
+// Shared memory (floats) of a map adjoint tile: phases 1-2 use the moments, W, Q, QW,
+// the pivots, the primary-term sums and one m of H; phase 3 keeps the moments (then
+// h) and the warps' row buffers.
+__host__ __device__ inline size_t bwd_tile_floats_rt(int K, int mr) {
+    const size_t a = (size_t)K * (mr + 1) * 2 * TILE;
+    const size_t p12 = a + 3 * (size_t)K * TILE + 2 * TILE + TILE + (size_t)K * K * 2;
+    const size_t p3 = a + (size_t)NWARPS * ROW;
+    return p12 > p3 ? p12 : p3;
+}
+
 // Device status bits.
 constexpr int ST_BAD_TILE = 1;
 constexpr int ST_ROW_OVERFLOW = 2;   // informational: a row wider than the warp buffer used direct global adds

@@ -208,6 +208,14 @@ class Plan:
         check(lib().tpcf_plan_sync(self._h), "tpcf_plan_sync")
 
 
+def probe_fp32_peak(stream=None) -> Tuple[float, float]:
+    """Measured FP32-pipe throughput of the current device in TFLOP/s: (scalar FMA,
+    packed f32x2 FMA) (tpcf_probe_fp32_peak)."""
+    out = (ctypes.c_double * 2)()
+    check(lib().tpcf_probe_fp32_peak(out, _stream_ptr(stream)), "tpcf_probe_fp32_peak")
+    return float(out[0]), float(out[1])
+
+
 def as_complex(zeta: torch.Tensor) -> torch.Tensor:
     """(M+1,K,K,2) float64 -> (M+1,K,K) complex128 view."""
     return torch.view_as_complex(zeta)

@@ -61,8 +61,8 @@ def test_batch_forward_matches_single_calls_and_oracle():
         zs.append(z)
         ns.append(n)
     b = tpcf.Batch(plans, ds, ws, zs, ns)
-    # groups by (M, self-pair mode): 5 distinct here -> pack, zero, 5 pair kernels, reduce, finalize
-    assert b.kernel_launches() == 2 + 5 + 2
+    # one persistent pair kernel for every plan: pack, zero, forward, reduce, finalize
+    assert b.kernel_launches() == 5
     for replay in range(2):
         for z in zs:
             z.fill_(float("nan"))
@@ -106,7 +106,8 @@ def test_batch_adjoint_matches_single_calls():
         dls.append(g)
         gs.append(torch.full((12 * nside * nside,), float("nan"), dtype=torch.float32, device="cuda:0"))
     b = tpcf.Batch(plans, ds, ws, zs, ns, dls, gs)
-    assert b.kernel_launches() == 2 + 4 + 2 + 1 + 4
+    # pack, zero, forward, reduce, finalize, adjoint coefficients, adjoint
+    assert b.kernel_launches() == 7
     b.launch()
     torch.cuda.synchronize()
     for i, p in enumerate(plans):
@@ -141,3 +142,62 @@ def test_batch_rejects_bad_members():
     with pytest.raises(tpcf.TpcfError) as e:
         tpcf.Batch([q], [dd], [wd], [z], [n], [g], [gr])
     assert e.value.status == 5
+
+
+def test_batch_members_of_the_mixed_nside_workload():
+    """The first four maps of the 64-map batched workload (Nside 256, 512, 1024, 2048,
+    their own bins and m_max) at full size, forward + adjoint in one graph replay:
+    every zeta equals the single-call forward, the two smaller maps' gradients equal
+    the single-call adjoint, and the Nside 2048 member matches the oracle on sampled
+    pivots of the belt and of a polar cap."""
+    import math
+    tpcf = _tpcf()
+    wls = synth.batched_maps(64)[:4]
+    assert [wl.nside for wl in wls] == [256, 512, 1024, 2048]
+    plans, ds, ws, zs, ns, dls, gs, host = [], [], [], [], [], [], [], []
+    for wl in wls:
+        K, M = wl.bins.nbins, wl.bins.m_max
+        d = wl.delta().astype(np.float32)
+        w = wl.weights().astype(np.float32)
+        host.append((d, w))
+        p = tpcf.Plan.map(wl.nside, wl.bins.edges_deg, M)
+        plans.append(p)
+        ds.append(to_dev(d))
+        ws.append(to_dev(w))
+        z, n = _outs(p)
+        zs.append(z)
+        ns.append(n)
+        g = torch.zeros((M + 1, K, K, 2), dtype=torch.float64, device="cuda:0")
+        g[..., 0] = torch.from_numpy(wl.cotangent()).to("cuda:0")
+        dls.append(g)
+        gs.append(torch.full((12 * wl.nside ** 2,), float("nan"), dtype=torch.float32, device="cuda:0"))
+    b = tpcf.Batch(plans, ds, ws, zs, ns, dls, gs)
+    b.launch()
+    torch.cuda.synchronize()
+    for i, p in enumerate(plans):
+        p.sync()
+        z1, n1 = p.forward(ds[i], ws[i])
+        torch.cuda.synchronize()
+        zb = tpcf.as_complex(zs[i]).cpu().numpy()
+        zo = tpcf.as_complex(z1).cpu().numpy()
+        assert np.isfinite(zb).all()
+        assert rel_err_per_m(zb, zo).max() < 1e-6, i
+        if i < 2:
+            g1 = p.backward(ds[i], ws[i], n1, dls[i]).cpu().numpy()
+            gb = gs[i].cpu().numpy()
+            assert np.abs(gb - g1).max() <= 1e-5 * np.abs(g1).max(), i
+    # Nside 2048 member: single calls on sampled pivots against the oracle
+    wl, p = wls[3], plans[3]
+    d, w = host[3]
+    n = wl.nside
+    from test_gpu_fullsize import oracle_on_band, ring_first
+    for r in ((5 * n) // 4, 40):
+        lo = ring_first(n, r)
+        hi = lo + 160
+        zg, _ = p.forward(ds[3], ws[3], (lo, hi))
+        ref, _ = oracle_on_band(n, d, w, wl.bins.edges_deg, wl.bins.m_max, lo, hi, r, r)
+        assert ref["min_margin"] > 1e-12
+        assert rel_err_per_m(tpcf.as_complex(zg).cpu().numpy(), ref["zeta"]).max() < TOL, r
+    b.close()
+    for p in plans:
+        p.close()
