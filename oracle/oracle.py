@@ -285,6 +285,34 @@ def pair_counts(xyz, edges_deg, pivots=None) -> np.ndarray:
     return out
 
 
+# --------------------------------------------------------------- multi-field
+
+def zeta_multi(xyz, fields, edges_deg, m_max: int, pivots=None):
+    """Estimator of three scalar fields A, B, C sampled at the same points (end of
+    section 2, after eq. ubEstimator): a pivot field is chosen and the result summed
+    over the cyclic permutations of {A, B, C}.  With pivot field P and neighbour fields
+    X (first separation bin k1) and Y (second bin k2), the pre-cyclic sums are
+        S^{P;XY}_m(k1,k2) = sum_i w^P_i P_i a_m^{k1}(i; X) conj(a_m^{k2}(i; Y)),
+        D^{P;XY}(k1,k2)   = sum_i w^P_i W^{k1}(i; X) W^{k2}(i; Y),
+    with a(i; X) = sum_j w^X_j X_j e^{-i m phi_ij} and W(i; X) = sum_j w^X_j over the
+    bin (the moments of eq. Xm.binned for field X).  Then
+        S^{ABC} = S^{A;BC} + S^{B;CA} + S^{C;AB},  D^{ABC} likewise (the same sum with
+        every field set to 1, m = 0),  zeta^{ABC} = S^{ABC} / D^{ABC}  (reading R3).
+    ``fields`` = ((d_A, w_A), (d_B, w_B), (d_C, w_C)).  S, D and zeta are full K x K
+    arrays (not Hermitian unless B = C)."""
+    moms = [moments(xyz, d, w, edges_deg, m_max, pivots) for d, w in fields]
+    piv = moms[0]["pivots"]
+    S = 0.0
+    D = 0.0
+    for P, X, Y in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        dP, wP = _f64(fields[P][0]), _f64(fields[P][1])
+        S = S + np.einsum("i,ikm,ilm->mkl", wP[piv] * dP[piv], moms[X]["a"], np.conj(moms[Y]["a"]))
+        D = D + np.einsum("i,ik,il->kl", wP[piv], moms[X]["W"], moms[Y]["W"])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        zeta = np.where(D[None] != 0, S / np.where(D == 0, 1.0, D)[None], 0.0)
+    return dict(S=S, D=D, zeta=zeta, pairs=moms[0]["pairs"], min_margin=moms[0]["min_margin"])
+
+
 # ------------------------------------------------------------- catalogue D-R
 
 def catalog_zeta(xyz_d, w_d, xyz_r, edges_deg, m_max: int, pivots_d=None, pivots_r=None):
