@@ -47,7 +47,7 @@ sys.path.insert(0, ROOT)
 METRIC = "neighbour pairs/s; Nside=4096 ζ_m time fwd & fwd+bwd at stated err vs FP64"
 FP32_LANES_PER_SM = 128
 MAP_WORKLOADS = ("fullsky_nside4096", "masked_map_nside1024", "fullsky_nside512", "map_nside64",
-                 "fullsky_nside4096_paper")
+                 "fullsky_nside4096_paper", "fullsky_nside2048")
 # The paper's exact-path timing (Sec. 3.2): ~40 min for one Nside 4096 map, 20 log bins over
 # 8-200 arcmin, m <= 8, forward only, one 128-thread CPU node; with the 3.42e13 in-bin
 # pairs of that shape (N^2 (cos 8' - cos 200') / 2) that is 1.43e10 pairs/s.

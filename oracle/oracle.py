@@ -297,7 +297,7 @@ def zeta_multi(xyz, fields, edges_deg, m_max: int, pivots=None):
     with a(i; X) = sum_j w^X_j X_j e^{-i m phi_ij} and W(i; X) = sum_j w^X_j over the
     bin (the moments of eq. Xm.binned for field X).  Then
         S^{ABC} = S^{A;BC} + S^{B;CA} + S^{C;AB},  D^{ABC} likewise (the same sum with
-        every field set to 1, m = 0),  zeta^{ABC} = S^{ABC} / D^{ABC}  (reading R3).
+        every field set to 1, m = 0),  zeta^{ABC} = S^{ABC} / D^{ABC}  (the normalisation contract(norm="R3") applies).
     ``fields`` = ((d_A, w_A), (d_B, w_B), (d_C, w_C)).  S, D and zeta are full K x K
     arrays (not Hermitian unless B = C)."""
     moms = [moments(xyz, d, w, edges_deg, m_max, pivots) for d, w in fields]

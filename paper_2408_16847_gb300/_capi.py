@@ -25,7 +25,7 @@ EXPORTS = ["tpcf_status_string", "tpcf_last_error", "tpcf_plan_create_map", "tpc
            "tpcf_batch_launch", "tpcf_batch_kernel_launches", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync", "tpcf_normalize",
            "tpcf_plan_destroy", "tpcf_test_fail_allocation", "tpcf_test_live_allocations",
            "tpcf_plan_halo", "tpcf_plan_autotune", "tpcf_plan_launch_config", "tpcf_plan_set_launch_config",
-           "tpcf_probe_fp32_peak"]
+           "tpcf_probe_fp32_peak", "tpcf_forward_multi"]
 
 
 class TpcfError(RuntimeError):
@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
     L.tpcf_plan_launch_config.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
     L.tpcf_plan_set_launch_config.restype = ctypes.c_int
     L.tpcf_plan_set_launch_config.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+    L.tpcf_forward_multi.restype = ctypes.c_int
+    L.tpcf_forward_multi.argtypes = [_vp] + [_vp] * 6 + [_i64, _i64, _vp, _vp, _vp, _vp]
     L.tpcf_probe_fp32_peak.restype = ctypes.c_int
     L.tpcf_probe_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
     L.tpcf_plan_halo.restype = ctypes.c_int

@@ -17,6 +17,29 @@ using namespace tpcf;
 
 namespace tpcf {
 // per-M launchers (map_inst.cu)
+#define TPCF_DECL_MULTI(m)                                                                                    \
+    cudaError_t map_fwd_multi_launch_m##m(const MapDev&, const MapCall&, const float2*, const float2*, int, \
+                                          cudaStream_t);                                                  \
+    int map_fwd_multi_occupancy_m##m(int);
+TPCF_DECL_MULTI(0) TPCF_DECL_MULTI(1) TPCF_DECL_MULTI(2) TPCF_DECL_MULTI(3) TPCF_DECL_MULTI(4) TPCF_DECL_MULTI(5)
+TPCF_DECL_MULTI(6) TPCF_DECL_MULTI(7) TPCF_DECL_MULTI(8) TPCF_DECL_MULTI(9) TPCF_DECL_MULTI(10)
+TPCF_DECL_MULTI(11) TPCF_DECL_MULTI(12) TPCF_DECL_MULTI(13) TPCF_DECL_MULTI(14) TPCF_DECL_MULTI(15)
+TPCF_DECL_MULTI(16)
+#undef TPCF_DECL_MULTI
+typedef cudaError_t (*multi_fn)(const MapDev&, const MapCall&, const float2*, const float2*, int, cudaStream_t);
+static const multi_fn kMulti[TPCF_MAX_M + 1] = {
+    map_fwd_multi_launch_m0,  map_fwd_multi_launch_m1,  map_fwd_multi_launch_m2,  map_fwd_multi_launch_m3,
+    map_fwd_multi_launch_m4,  map_fwd_multi_launch_m5,  map_fwd_multi_launch_m6,  map_fwd_multi_launch_m7,
+    map_fwd_multi_launch_m8,  map_fwd_multi_launch_m9,  map_fwd_multi_launch_m10, map_fwd_multi_launch_m11,
+    map_fwd_multi_launch_m12, map_fwd_multi_launch_m13, map_fwd_multi_launch_m14, map_fwd_multi_launch_m15,
+    map_fwd_multi_launch_m16};
+static int (*const kMultiOcc[TPCF_MAX_M + 1])(int) = {
+    map_fwd_multi_occupancy_m0,  map_fwd_multi_occupancy_m1,  map_fwd_multi_occupancy_m2,
+    map_fwd_multi_occupancy_m3,  map_fwd_multi_occupancy_m4,  map_fwd_multi_occupancy_m5,
+    map_fwd_multi_occupancy_m6,  map_fwd_multi_occupancy_m7,  map_fwd_multi_occupancy_m8,
+    map_fwd_multi_occupancy_m9,  map_fwd_multi_occupancy_m10, map_fwd_multi_occupancy_m11,
+    map_fwd_multi_occupancy_m12, map_fwd_multi_occupancy_m13, map_fwd_multi_occupancy_m14,
+    map_fwd_multi_occupancy_m15, map_fwd_multi_occupancy_m16};
 #define TPCF_DECL_M(m)                                                                         \
     cudaError_t map_fwd_launch_m##m(const MapDev&, const MapCall&, int, int, cudaStream_t);    \
     cudaError_t map_fwd_tc_launch_m##m(const MapDev&, const MapCall&, int, cudaStream_t);      \
@@ -410,6 +433,67 @@ extern "C" tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const 
     if (plan->kind == PLAN_CATALOG)
         return catalog_forward(plan, d_delta, d_w, pivot_begin, pivot_end, d_zeta, d_norm, d_sums, s);
     return TPCF_ERR_UNSUPPORTED;
+}
+
+extern "C" tpcf_status tpcf_forward_multi(tpcf_plan plan, const float* d_delta_a, const float* d_w_a,
+                                          const float* d_delta_b, const float* d_w_b, const float* d_delta_c,
+                                          const float* d_w_c, int64_t pivot_begin, int64_t pivot_end, double* d_zeta,
+                                          double* d_norm, double* d_sums, void* stream) {
+    if (!plan || !d_delta_a || !d_w_a || !d_delta_b || !d_w_b || !d_delta_c || !d_w_c || !d_zeta || !d_norm)
+        return TPCF_ERR_INVALID_ARG;
+    if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
+    tpcf_plan_s* P = plan;
+    if (P->kind != PLAN_MAP || (P->flags & (TPCF_CONTRACT_TC | TPCF_SELF_PAIRS_SUBTRACT))) {
+        set_error("tpcf_forward_multi: map plans with the FP32 contraction, self pairs kept");
+        return TPCF_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    P->last_stream = s;
+    const MapDev& g = P->map;
+    const int K = P->K, M = P->M;
+    const int nent = n_entries_multi(K, M);
+    if (!P->wdw_b) {
+        const int occ = kMultiOcc[M](K);
+        if (occ < 1) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "tpcf_forward_multi: three fields' moments (K=%d, m_max=%d) do not fit in shared memory", K, M);
+            return TPCF_ERR_UNSUPPORTED;
+        }
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)P->num_sms * occ));
+        float2 *b, *c;
+        double *sl, *su;
+        TRY_CUDA(P->alloc(&b, g.npix));
+        TRY_CUDA(P->alloc(&c, g.npix));
+        TRY_CUDA(P->alloc(&sl, (size_t)grid * nent));
+        TRY_CUDA(P->alloc(&su, (size_t)nent));
+        P->wdw_c = c;
+        P->mslots = sl;
+        P->msums = su;
+        P->multi_grid = grid;
+        P->wdw_b = b;
+    }
+    pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_delta_a, d_w_a, P->wdw, g.npix);
+    pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_delta_b, d_w_b, P->wdw_b, g.npix);
+    pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_delta_c, d_w_c, P->wdw_c, g.npix);
+    TRY_CUDA(cudaMemsetAsync(P->mslots, 0, sizeof(double) * (size_t)P->multi_grid * nent, s));
+    TRY_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(int), s));
+    MapCall c{};
+    c.wdw = P->wdw;
+    c.piv_lo = pivot_begin;
+    c.piv_hi = pivot_end;
+    c.slots = P->mslots;
+    c.counter = P->counter;
+    c.status = P->status;
+    c.flush = P->tune_fwd.flush;
+    tile_range(P, pivot_begin, pivot_end, &c.tile_lo, &c.tile_hi);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.tile_hi - c.tile_lo, P->multi_grid));
+    TRY_CUDA(kMulti[M](g, c, P->wdw_b, P->wdw_c, grid, s));
+    reduce_slots_kernel<<<n_blocks(nent, 128), 128, 0, s>>>(P->mslots, P->multi_grid, nent, P->msums);
+    const int nout = (M + 1) * K * K;
+    finalize_full_kernel<<<n_blocks(nout, 128), 128, 0, s>>>(P->msums, K, M, d_zeta, d_norm, d_sums);
+    P->launches += 6;  // three packs, the pair kernel, reduce, finalize
+    TRY_CUDA(cudaGetLastError());
+    return TPCF_OK;
 }
 
 extern "C" tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_t pivot_begin,

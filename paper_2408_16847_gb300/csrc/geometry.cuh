@@ -22,6 +22,7 @@ __global__ void pack_kernel(const float* delta, const float* w, float2* wdw, int
 __global__ void reduce_slots_kernel(const double* slots, int nslots, int nent, double* sums);
 __global__ void finalize_kernel(const double* sums, int K, int M, int self_subtract, double scale,
                                 double* zeta, double* norm, double* raw);
+__global__ void finalize_full_kernel(const double* sums, int K, int M, double* zeta, double* norm, double* raw);
 __global__ void adjoint_prep_kernel(const double* dL_dzeta, const double* norm, int K, int M, float* H,
                                     int with_diag);
 __global__ void zero_f32_kernel(float* p, int64_t n);

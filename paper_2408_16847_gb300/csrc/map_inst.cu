@@ -11,10 +11,19 @@
 
 namespace tpcf {
 
+// Every pair kernel asks for the largest shared-memory carveout: they are sized to fit
+// 2-3 CTAs per SM only with it (the occupancy queries below assume it as well).
+template <class Kern>
+static cudaError_t prefer_shared(Kern* k, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // Launch the pair kernel `k` with `smem` bytes of dynamic shared memory.
 template <class Kern>
 static cudaError_t launch(Kern* k, size_t smem, int grid, const MapDev& g, const MapCall& c, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prefer_shared(k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NTHREADS, smem, s>>>(g, c);
     return cudaGetLastError();
@@ -23,7 +32,7 @@ static cudaError_t launch(Kern* k, size_t smem, int grid, const MapDev& g, const
 template <class Kern>
 static int occupancy(Kern* k, size_t smem) {
     int nb = 0;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (prefer_shared(k, smem) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NTHREADS, smem) != cudaSuccess) return 0;
     return nb;
 }
@@ -78,12 +87,12 @@ cudaError_t TPCF_CAT(map_fwd_tc_launch_m, TPCF_M)(const MapDev& g, const MapCall
     const size_t smem = tc_smem_bytes(g.K, TPCF_M, c.self_subtract != 0);
     if (c.self_subtract) {
         auto* k = map_fwd_tc_kernel<TPCF_M, true>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = prefer_shared(k, smem);
         if (e != cudaSuccess) return e;
         k<<<grid, NTHREADS, smem, s>>>(g, c);
     } else {
         auto* k = map_fwd_tc_kernel<TPCF_M, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = prefer_shared(k, smem);
         if (e != cudaSuccess) return e;
         k<<<grid, NTHREADS, smem, s>>>(g, c);
     }
@@ -92,17 +101,25 @@ cudaError_t TPCF_CAT(map_fwd_tc_launch_m, TPCF_M)(const MapDev& g, const MapCall
 
 int TPCF_CAT(map_fwd_tc_occupancy_m, TPCF_M)(int K, int self_subtract) {
     const size_t smem = tc_smem_bytes(K, TPCF_M, self_subtract != 0);
-    int nb = 0;
-    if (self_subtract) {
-        cudaFuncSetAttribute(map_fwd_tc_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_tc_kernel<TPCF_M, true>, NTHREADS, smem);
-    } else {
-        cudaFuncSetAttribute(map_fwd_tc_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, map_fwd_tc_kernel<TPCF_M, false>, NTHREADS, smem);
-    }
+    const int nb = self_subtract ? occupancy(map_fwd_tc_kernel<TPCF_M, true>, smem)
+                                 : occupancy(map_fwd_tc_kernel<TPCF_M, false>, smem);
     // at most 512 / TC_TMEM_COLS accumulators per SM; more resident CTAs would wait in tcgen05.alloc
     return nb < 512 / TC_TMEM_COLS ? nb : 512 / TC_TMEM_COLS;
+}
+
+// Multi-field forward (three fields on the same pixels).
+cudaError_t TPCF_CAT(map_fwd_multi_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, const float2* wdwB,
+                                                     const float2* wdwC, int grid, cudaStream_t s) {
+    const size_t smem = multi_tile_floats(g.K, TPCF_M) * sizeof(float);
+    auto* k = map_fwd_multi_kernel<TPCF_M>;
+    cudaError_t e = prefer_shared(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(g, c, wdwB, wdwC);
+    return cudaGetLastError();
+}
+
+int TPCF_CAT(map_fwd_multi_occupancy_m, TPCF_M)(int K) {
+    return occupancy(map_fwd_multi_kernel<TPCF_M>, multi_tile_floats(K, TPCF_M) * sizeof(float));
 }
 
 // Forward that reads the caller's delta and w directly (no packed copy).
@@ -110,7 +127,7 @@ cudaError_t TPCF_CAT(map_fwd_direct_launch_m, TPCF_M)(const MapDev& g, const Map
                                                       cudaStream_t s) {
     const size_t smem = tile_floats<TPCF_M>(g.K) * sizeof(float);
     auto* k = map_fwd_kernel<TPCF_M, false, true>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prefer_shared(k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NTHREADS, smem, s>>>(g, c);
     return cudaGetLastError();
@@ -124,7 +141,7 @@ size_t TPCF_CAT(map_bwd_smem_m, TPCF_M)(int K) { return bwd_tile_floats<TPCF_M>(
 cudaError_t TPCF_CAT(batch_fwd_launch_m, TPCF_M)(const BatchItem* items, int n, long long total,
                                                  unsigned long long* counter, size_t smem, int grid, cudaStream_t s) {
     auto* k = batch_fwd_kernel<TPCF_M>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prefer_shared(k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
     return cudaGetLastError();
@@ -134,7 +151,7 @@ cudaError_t TPCF_CAT(batch_bwd_launch_m, TPCF_M)(const BatchItem* items, int n, 
                                                  unsigned long long* counter, size_t smem, int grid,
                                                  cudaStream_t s) {
     auto* k = batch_bwd_kernel<TPCF_M>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prefer_shared(k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NTHREADS, smem, s>>>(items, n, total, counter);
     return cudaGetLastError();
@@ -149,12 +166,12 @@ cudaError_t TPCF_CAT(cat_fwd_launch_m, TPCF_M)(const CatDev& g, const MapCall& c
     const size_t smem = cat_tile_bytes<TPCF_M>(g.K);
     if (c.self_subtract) {
         auto* k = cat_fwd_kernel<TPCF_M, true>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = prefer_shared(k, smem);
         if (e != cudaSuccess) return e;
         k<<<grid, NTHREADS, smem, s>>>(g, c);
     } else {
         auto* k = cat_fwd_kernel<TPCF_M, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = prefer_shared(k, smem);
         if (e != cudaSuccess) return e;
         k<<<grid, NTHREADS, smem, s>>>(g, c);
     }
@@ -163,22 +180,14 @@ cudaError_t TPCF_CAT(cat_fwd_launch_m, TPCF_M)(const CatDev& g, const MapCall& c
 
 int TPCF_CAT(cat_fwd_occupancy_m, TPCF_M)(int K, int self_subtract) {
     const size_t smem = cat_tile_bytes<TPCF_M>(K);
-    int nb = 0;
-    if (self_subtract) {
-        cudaFuncSetAttribute(cat_fwd_kernel<TPCF_M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cat_fwd_kernel<TPCF_M, true>, NTHREADS, smem);
-    } else {
-        cudaFuncSetAttribute(cat_fwd_kernel<TPCF_M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cat_fwd_kernel<TPCF_M, false>, NTHREADS, smem);
-    }
-    return nb;
+    return self_subtract ? occupancy(cat_fwd_kernel<TPCF_M, true>, smem) : occupancy(cat_fwd_kernel<TPCF_M, false>, smem);
 }
 
 // Catalogue adjoint.
 cudaError_t TPCF_CAT(cat_bwd_launch_m, TPCF_M)(const CatDev& g, const MapCall& c, int grid, cudaStream_t s) {
     const size_t smem = cat_bwd_bytes<TPCF_M>(g.K);
     auto* k = cat_bwd_kernel<TPCF_M>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prefer_shared(k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NTHREADS, smem, s>>>(g, c);
     return cudaGetLastError();
@@ -187,7 +196,7 @@ cudaError_t TPCF_CAT(cat_bwd_launch_m, TPCF_M)(const CatDev& g, const MapCall& c
 int TPCF_CAT(cat_bwd_occupancy_m, TPCF_M)(int K) {
     const size_t smem = cat_bwd_bytes<TPCF_M>(K);
     int nb = 0;
-    cudaFuncSetAttribute(cat_bwd_kernel<TPCF_M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prefer_shared(cat_bwd_kernel<TPCF_M>, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cat_bwd_kernel<TPCF_M>, NTHREADS, smem);
     return nb;
 }

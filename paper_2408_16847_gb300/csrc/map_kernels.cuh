@@ -1249,6 +1249,122 @@ __global__ void __launch_bounds__(NTHREADS, 2) batch_fwd_kernel(const BatchItem*
     }
 }
 
+// ------------------------------------------------------------ multi-field
+// Three fields A, B, C on the same pixels (end of Sec. 2, after eq. ubEstimator): a
+// tile accumulates the moments a^k(i; F), W^k(i; F) of every field F in its own block
+// of shared memory (three passes of the single-field walk), then adds, over the
+// cyclic permutations (P, X, Y) of (A, B, C),
+//     S_m(k1,k2) += sum_i w^P_i P_i a_m^{k1}(i; X) conj(a_m^{k2}(i; Y)),
+//     D(k1,k2)   += sum_i w^P_i W^{k1}(i; X) W^{k2}(i; Y),
+// into the CTA's FP64 slot.  These sums are not Hermitian: the slot holds the full
+// K x K matrices, for m, for (k1, k2): (Re S, Im S); then D for (k1, k2).
+__host__ __device__ inline size_t multi_field_floats(int K, int M) { return (size_t)K * (M + 1) * 2 * TILE + (size_t)K * TILE; }
+__host__ __device__ inline size_t multi_tile_floats(int K, int M) { return 3 * multi_field_floats(K, M) + 6 * TILE; }
+
+template <int M>
+__device__ __forceinline__ void tile_contract_multi(int K, const float* sF, const float* sPiv, double* slot) {
+    const size_t fsz = multi_field_floats(K, M);
+    const int KK = K * K;
+    const int nS = (M + 1) * KK;
+    const int cyc[3][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}};
+    for (int e = threadIdx.x; e < nS + KK; e += NTHREADS) {
+        if (e < nS) {
+            const int m = e / KK, r = e - m * KK, k1 = r / K, k2 = r - k1 * K;
+            float sr = 0.0f, si = 0.0f;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const float* wd = sPiv + cyc[t][0] * 2 * TILE;
+                const float* r1 = sF + cyc[t][1] * fsz + ((size_t)k1 * (M + 1) + m) * 2 * TILE;
+                const float* i1 = r1 + TILE;
+                const float* r2 = sF + cyc[t][2] * fsz + ((size_t)k2 * (M + 1) + m) * 2 * TILE;
+                const float* i2 = r2 + TILE;
+#pragma unroll 8
+                for (int j = 0; j < TILE; ++j) {
+                    const int l = (j + threadIdx.x) & (TILE - 1);
+                    const float a = r1[l], b = i1[l], cc = r2[l], d = i2[l];
+                    sr = fmaf(wd[l], fmaf(a, cc, b * d), sr);
+                    si = fmaf(wd[l], fmaf(a, d, -b * cc), si);
+                }
+            }
+            atomicAdd(slot + 2 * e, (double)sr);
+            atomicAdd(slot + 2 * e + 1, (double)si);
+        } else {
+            const int idx = e - nS, k1 = idx / K, k2 = idx - k1 * K;
+            float sd = 0.0f;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const float* wt = sPiv + cyc[t][0] * 2 * TILE + TILE;
+                const float* W1 = sF + cyc[t][1] * fsz + (size_t)K * (M + 1) * 2 * TILE + k1 * TILE;
+                const float* W2 = sF + cyc[t][2] * fsz + (size_t)K * (M + 1) * 2 * TILE + k2 * TILE;
+                for (int j = 0; j < TILE; ++j) {
+                    const int l = (j + threadIdx.x) & (TILE - 1);
+                    sd = fmaf(wt[l], W1[l] * W2[l], sd);
+                }
+            }
+            atomicAdd(slot + 2 * nS + idx, (double)sd);
+        }
+    }
+}
+
+// The multi-field forward: c.wdw holds (w d, w) of field A, wdwB and wdwC those of
+// B and C.  One tile at a time, as map_fwd_kernel.
+template <int M>
+__global__ void __launch_bounds__(NTHREADS, 2) map_fwd_multi_kernel(MapDev g, MapCall c,
+                                                                    const float2* __restrict__ wdwB,
+                                                                    const float2* __restrict__ wdwC) {
+    extern __shared__ float smem[];
+    __shared__ int s_tile;
+    const int K = g.K;
+    const size_t fsz = multi_field_floats(K, M);
+    float* sF = smem;
+    float* sPiv = smem + 3 * fsz;  // [field][w d, w][32]
+    double* slot = c.slots + (size_t)blockIdx.x * n_entries_multi(K, M);
+    const int lane = threadIdx.x & 31;
+    const float2* arr[3] = {c.wdw, wdwB, wdwC};
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
+        __syncthreads();
+        const long long tile = c.tile_lo + s_tile;
+        if (tile >= c.tile_hi) break;
+        const int2 tq = g.tiles[tile];
+        if (tq.x < 0 || tq.x >= g.nrings) {
+            if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
+            __syncthreads();
+            continue;
+        }
+        const PivotRing P = pivot_ring(g, tq.x);
+        const int q = tq.y + lane;
+        const long long pix = g.ring_first[P.i] + q;
+        const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+        float2 pv[3];
+        bool live = false;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            pv[f] = in ? arr[f][pix] : make_float2(0.0f, 0.0f);
+            live = live || pv[f].y != 0.0f;
+        }
+        const int qg = min(q, P.n_i - 1);
+        if (!__syncthreads_or(live)) continue;
+        for (size_t e = threadIdx.x; e < 3 * fsz; e += NTHREADS) sF[e] = 0.0f;
+        if (threadIdx.x < TILE) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                sPiv[f * 2 * TILE + lane] = pv[f].x;
+                sPiv[f * 2 * TILE + TILE + lane] = pv[f].y;
+            }
+        }
+        __syncthreads();
+        for (int f = 0; f < 3; ++f) {
+            float* sA = sF + f * fsz;
+            tile_moments<M, false>(g, P, qg, PackedLoad{arr[f]}, sA, sA + (size_t)K * (M + 1) * 2 * TILE, nullptr,
+                                   nullptr, c.flush);
+        }
+        __syncthreads();
+        tile_contract_multi<M>(K, sF, sPiv, slot);
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- pair count
 #if defined(TPCF_M) && TPCF_M == 0  // one definition, in the M = 0 object
 // counts[0] += in-bin ordered pairs (i, j) of the pivots with w_i != 0 (any w_j);

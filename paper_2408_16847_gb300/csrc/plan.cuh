@@ -56,6 +56,12 @@ struct tpcf_plan_s {
     int* counter = nullptr;
     int* status = nullptr;
     float* H = nullptr;
+    // multi-field forward (allocated on its first call): packed fields B and C, slots
+    float2* wdw_b = nullptr;
+    float2* wdw_c = nullptr;
+    double* mslots = nullptr;
+    double* msums = nullptr;
+    int multi_grid = 0;
     // staging for tpcf_run_host
     float* st_delta = nullptr;
     float* st_w = nullptr;

@@ -65,6 +65,26 @@ __device__ __forceinline__ void finalize_one(const double* __restrict__ sums, in
     if (m == 0) norm[rem] = d;
 }
 
+// Multi-field estimate: zeta_m(k1,k2) = S_m(k1,k2) / D(k1,k2) over full K x K sums
+// (no Hermitian fill: the cyclic three-field sums are not Hermitian); zeta = 0 where
+// D = 0.  One output entry idx = (m, k1, k2) per thread.
+__global__ void finalize_full_kernel(const double* __restrict__ sums, int K, int M, double* zeta, double* norm,
+                                     double* raw) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int KK = K * K, nS = (M + 1) * KK;
+    if (idx >= nS) return;
+    const int r = idx % KK;
+    const double D = sums[2 * nS + r];
+    const double sr = sums[2 * idx], si = sums[2 * idx + 1];
+    zeta[2 * idx] = D != 0.0 ? sr / D : 0.0;
+    zeta[2 * idx + 1] = D != 0.0 ? si / D : 0.0;
+    if (raw) {
+        raw[2 * idx] = sr;
+        raw[2 * idx + 1] = si;
+    }
+    if (idx < KK) norm[idx] = D;
+}
+
 __global__ void finalize_kernel(const double* __restrict__ sums, int K, int M, int self_subtract,
                                 double scale, double* zeta, double* norm, double* raw) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;

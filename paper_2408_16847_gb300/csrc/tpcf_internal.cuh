@@ -98,6 +98,8 @@ inline __host__ __device__ int n_pairs_tri(int K) { return K * (K + 1) / 2; }
 inline __host__ __device__ int n_entries(int K, int M) {
     return 2 * (M + 1) * n_pairs_tri(K) + n_pairs_tri(K) + 2 * K;
 }
+// Entries of the multi-field partial sums: full K x K matrices, S (complex) per m, then D.
+inline __host__ __device__ int n_entries_multi(int K, int M) { return 2 * (M + 1) * K * K + K * K; }
 
 constexpr int ROW = 512;  // floats per warp row buffer of the adjoint (wider rows: whole-ring or global adds)
 

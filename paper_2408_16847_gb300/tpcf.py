@@ -116,6 +116,28 @@ class Plan:
             return zeta, norm, sums
         return zeta, norm
 
+    def forward_multi(self, fields, pivots: Optional[Tuple[int, int]] = None, want_sums: bool = False,
+                      stream=None):
+        """Three-field estimate zeta^{ABC} (tpcf_forward_multi): ``fields`` =
+        ((delta_A, w_A), (delta_B, w_B), (delta_C, w_C)) float32 CUDA tensors.  Returns
+        (zeta (M+1,K,K,2) float64, norm (K,K)[, sums]); full K x K matrices."""
+        n = self.npoints
+        ptrs = []
+        for name, (d, w) in zip("ABC", fields):
+            _need(d, torch.float32, n, "delta_" + name)
+            _need(w, torch.float32, n, "w_" + name)
+            ptrs += [_ptr(d), _ptr(w)]
+        lo, hi = (0, n) if pivots is None else (int(pivots[0]), int(pivots[1]))
+        dev = fields[0][0].device
+        zeta = torch.empty(self.zeta_shape(), dtype=torch.float64, device=dev)
+        norm = torch.empty((self.K, self.K), dtype=torch.float64, device=dev)
+        sums = torch.empty(self.zeta_shape(), dtype=torch.float64, device=dev) if want_sums else None
+        check(lib().tpcf_forward_multi(self._h, *ptrs, lo, hi, _ptr(zeta), _ptr(norm), _ptr(sums),
+                                       _stream_ptr(stream)), "tpcf_forward_multi")
+        if want_sums:
+            return zeta, norm, sums
+        return zeta, norm
+
     def backward(self, delta: torch.Tensor, w: torch.Tensor, norm: torch.Tensor, dL_dzeta: torch.Tensor,
                  pivots: Optional[Tuple[int, int]] = None, stream=None) -> torch.Tensor:
         """dL/d(delta) (float32, npoints) given dL/dzeta (M+1,K,K,2) float64 and the forward's norm."""

@@ -222,6 +222,13 @@ def fullsky_nside4096_paper() -> MapWorkload:
                        (0.05, 1.0), seed=BASE_SEED + 5, cot_seed=BASE_SEED + 107)
 
 
+def fullsky_nside2048() -> MapWorkload:
+    """The full-sky recipe at Nside 2048 (bumps scaled by pixel count: 250,000): the
+    case profiled with ncu at the full recipe's neighbour density per bin."""
+    return MapWorkload("fullsky_nside2048", 2048, log_bins(0.1, 2.0, 20, 10), 250_000, (0.05, 1.0),
+                       seed=BASE_SEED + 8, cot_seed=BASE_SEED + 108)
+
+
 def fullsky_nside512() -> MapWorkload:
     """The full-sky recipe at Nside 512 (bumps scaled by pixel count: 15,625): the
     small case profiled in place of the Nside 4096 map."""

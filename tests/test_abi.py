@@ -19,7 +19,7 @@ def lib():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "tpcf.h")).read()
-    return sorted(set(re.findall(r"\b(tpcf_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(tpcf_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_what_binding_lists():
