@@ -337,3 +337,60 @@ def catalog_zeta(xyz_d, w_d, xyz_r, edges_deg, m_max: int, pivots_d=None, pivots
     with np.errstate(divide="ignore", invalid="ignore"):
         z = np.where(DR[None] != 0, u["S"] / np.where(DR == 0, 1.0, DR)[None], 0.0)
     return dict(S=u["S"], D=DR, zeta=z, alpha=alpha, pairs=u["pairs"] + r["pairs"])
+
+
+# ------------------------------------------------------------------ m-coupling
+
+def _hermitian_ext(X, n: int):
+    """X_n for any integer n from X_0..X_N, with X_{-n} = conj(X_n) (real field)."""
+    return X[n] if n >= 0 else np.conj(X[-n])
+
+
+def edge_correct(S, R, scale: float = 1.0):
+    """m-coupling (edge) correction of a data-minus-randoms estimate (the paper leaves
+    masks and survey geometry for later; the reading used here is the standard one for
+    harmonic 3PCF estimators).
+
+    For one pair of bins the triplet counts are densities in the angle phi between the
+    two neighbours, N(phi) for the (D - R) field and R(phi) for the randoms with d = 1,
+    and the estimate of the 3PCF is the ratio zeta(phi) = N(phi) / R(phi).  With
+    X_n = integral of X(phi) e^{-i n phi} (the raw sums S_n of the estimator, S_{-n} =
+    conj(S_n)) and zeta(phi) = sum_m z_m e^{i m phi}, the product becomes a convolution:
+        S_m = sum_{m'} z_{m'} scale R_{m - m'},        m = -M..M,
+    truncated to |m'| <= M (it needs R_n for n = 0..2M).  ``S`` (M+1, K, K) complex
+    (m = 0..M, the D - R run), ``R`` (>= 2M+1, K, K) complex (the randoms' d = 1 run),
+    ``scale`` the randoms' normalisation (alpha^3 in the D - R reading).  Solves the
+    (2M+1) system per (k1, k2) with numpy.linalg.solve; returns z (M+1, K, K) for
+    m = 0..M, 0 where R_0(k1, k2) = 0.  With R_n = 0 for n != 0 (no coupling) this is
+    S_m / (scale R_0).
+    """
+    S = np.asarray(S, dtype=complex)
+    R = np.asarray(R, dtype=complex)
+    M = S.shape[0] - 1
+    K = S.shape[1]
+    if R.shape[0] < 2 * M + 1:
+        raise ValueError("R needs multipoles 0..2M")
+    ms = np.arange(-M, M + 1)
+    z = np.zeros((M + 1, K, K), dtype=complex)
+    for k1 in range(K):
+        for k2 in range(K):
+            r = R[:, k1, k2]
+            if r[0] == 0:
+                continue
+            A = np.array([[scale * _hermitian_ext(r, m - mp) for mp in ms] for m in ms])
+            b = np.array([_hermitian_ext(S[:, k1, k2], m) for m in ms])
+            z[:, k1, k2] = np.linalg.solve(A, b)[M:]
+    return z
+
+
+def catalog_zeta_coupled(xyz_d, w_d, xyz_r, edges_deg, m_max: int, pivots_d=None, pivots_r=None):
+    """The D - R catalogue estimate with the m-coupling correction: S from the union
+    (as catalog_zeta) at multipoles 0..m_max, R from the randoms' d = 1 run at 0..2 m_max,
+    then edge_correct(S, R, alpha^3)."""
+    nd, nr = len(xyz_d), len(xyz_r)
+    alpha = float(np.sum(w_d)) / float(nr)
+    u = catalog_zeta(xyz_d, w_d, xyz_r, edges_deg, m_max, pivots_d, pivots_r)
+    pr = np.arange(nr) if pivots_r is None else _i64a(pivots_r)
+    r = zeta(_f64(xyz_r), np.ones(nr), np.ones(nr), edges_deg, 2 * m_max, pr)
+    z = edge_correct(u["S"], r["S"], alpha ** 3)
+    return dict(S=u["S"], R=r["S"], zeta=z, alpha=alpha, zeta_uncorrected=u["zeta"])
