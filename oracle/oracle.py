@@ -394,3 +394,59 @@ def catalog_zeta_coupled(xyz_d, w_d, xyz_r, edges_deg, m_max: int, pivots_d=None
     r = zeta(_f64(xyz_r), np.ones(nr), np.ones(nr), edges_deg, 2 * m_max, pr)
     z = edge_correct(u["S"], r["S"], alpha ** 3)
     return dict(S=u["S"], R=r["S"], zeta=z, alpha=alpha, zeta_uncorrected=u["zeta"])
+
+
+# ------------------------------------------------------------------ shared neighbour lists
+
+def ring_pixels(nside: int):
+    """(first pixel, pixel count) of each iso-latitude ring of the HEALPix RING scheme,
+    north to south (4 nside - 1 rings; Gorski et al. 2005)."""
+    out = []
+    first = 0
+    for r in range(1, 4 * nside):
+        n = 4 * r if r < nside else (4 * nside if r <= 3 * nside else 4 * (4 * nside - r))
+        out.append((first, n))
+        first += n
+    return out
+
+
+def pivot_groups(nside: int, group: int):
+    """Each ring's pixels cut into consecutive runs of `group` (the last run of a ring
+    shorter); returns (representatives, member lists), the representative of a run being
+    its middle pixel, first + (length - 1) // 2."""
+    reps, members = [], []
+    for first, n in ring_pixels(nside):
+        for s in range(0, n, group):
+            ln = min(group, n - s)
+            reps.append(first + s + (ln - 1) // 2)
+            members.append(np.arange(first + s, first + s + ln))
+    return np.asarray(reps, dtype=np.int64), members
+
+
+def zeta_grouped(nside: int, delta, w, edges_deg, m_max: int, group: int, pivots=None):
+    """The estimator with shared neighbour lists (Sec. 3.2: pivots very close to one
+    another share one neighbour list).  Reading used: the pixels of a ring are cut into
+    runs of `group` consecutive pixels (pivot_groups) and every pivot i of a run takes
+    the moments of the run's representative rho(i), neighbours and angles both:
+        S_m(k1,k2) = sum_i w_i d_i a_m^{k1}(rho(i)) conj(a_m^{k2}(rho(i))),
+        D(k1,k2)   = sum_i w_i W^{k1}(rho(i)) W^{k2}(rho(i)),   zeta = S / D,
+    over the pivots i in ``pivots`` (default all).  group = 1 is the exact estimator.
+    The moments of each representative are those of eq. Xm.binned (all other pixels in
+    the bins, the group's own members included)."""
+    xyz = pix2vec_ring(nside)
+    delta, w = _f64(delta), _f64(w)
+    npix = 12 * nside * nside
+    use = np.zeros(npix, dtype=bool)
+    use[np.arange(npix) if pivots is None else _i64a(pivots)] = True
+    reps, members = pivot_groups(nside, group)
+    wd = np.array([np.sum((w * delta)[m[use[m]]]) for m in members])
+    wt = np.array([np.sum(w[m[use[m]]]) for m in members])
+    live = np.array([bool(np.any(use[m])) for m in members])
+    reps, wd, wt = reps[live], wd[live], wt[live]
+    mom = moments(xyz, delta, w, edges_deg, m_max, reps)
+    a, W = mom["a"], mom["W"]
+    S = np.einsum("i,ikm,ilm->mkl", wd, a, np.conj(a))
+    D = np.einsum("i,ik,il->kl", wt, W, W)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        z = np.where(D[None] != 0, S / np.where(D == 0, 1.0, D)[None], 0.0)
+    return dict(S=S, D=D, zeta=z, reps=reps, min_margin=mom["min_margin"])
