@@ -65,6 +65,21 @@ typedef enum {
                                         TF32x3 operands, FP32 accumulate): map plans,
                                         tpcf_forward only; catalogue plans, batches and
                                         tpcf_forward_noalloc return UNSUPPORTED     */
+/* Normalisation.  The default divides by the weight triple sum of the same pivots:
+ * zeta_m = S_m / D with D(k1,k2) = sum_i w_i W^{k1}(i) W^{k2}(i).  The two flags below
+ * instead normalise each pivot's moments before the sum over pivots (Sec. 3.1): the
+ * prefactor of eq. Xm.binned divides a_m^k(i) by the weight of all the pivot's
+ * neighbours, sum_k W^k(i) (PIVOT_TOTAL); the binning figure's caption averages over
+ * the points of each bin, a_m^k(i) / W^k(i) (BIN_MEAN).  With X^k(i) the normalised
+ * moments (0 where the divisor is 0),
+ *   zeta_m(k1,k2) = sum_i w_i d_i X_m^{k1}(i) conj(X_m^{k2}(i)) / sum_i w_i,
+ * and d_norm holds sum_i w_i in every entry.  For tpcf_forward (map and catalogue
+ * plans) and tpcf_forward_noalloc; with TPCF_SELF_PAIRS_SUBTRACT or TPCF_CONTRACT_TC
+ * the plan is not created (UNSUPPORTED); tpcf_backward, batches and
+ * tpcf_forward_multi return UNSUPPORTED, and tpcf_plan_autotune tunes the forward
+ * only.  At most one of the two flags (else INVALID_ARG). */
+#define TPCF_NORM_BIN_MEAN 4u
+#define TPCF_NORM_PIVOT_TOTAL 8u
 
 #define TPCF_MAX_BINS 32
 #define TPCF_MAX_M 16
@@ -120,6 +135,26 @@ tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_xyz, int64_
 tpcf_status tpcf_normalize(const double* d_sums, const double* d_norm, double scale, int32_t nbins,
                            int32_t m_max, double* d_zeta, void* stream);
 
+/*
+ * m-coupling (edge) correction of a data-minus-randoms estimate: masks and survey
+ * geometry couple the multipoles (the paper leaves this for later work; Sec. 3.1 gives
+ * the harmonic decomposition it acts on).  For a bin pair the estimate is the ratio
+ * zeta(phi) = N(phi) / R(phi) of the triplet-angle densities of the D - R field and of
+ * the randoms; in harmonic space, with X_{-n} = conj(X_n) and
+ * zeta(phi) = sum_m z_m e^{i m phi},
+ *     S_m = sum_{m'=-M..M} z_{m'} scale R_{m-m'},    m = -M..M,
+ * which is solved per (k1, k2) by Gaussian elimination with partial pivoting (FP64)
+ * for z_m, m = 0..m_max.  d_sums: the raw sums S of the D - R run, (m_max+1) x K x K
+ * x {re, im} doubles (the zeta layout); d_rsums: the raw sums of the randoms' delta = 1
+ * run at multipoles 0..2 m_max, (2 m_max+1) x K x K x {re, im}; scale: alpha^3 as in
+ * tpcf_normalize; d_zeta: (m_max+1) x K x K x {re, im} (device, caller owned).  With
+ * no coupling (R_n = 0 for n != 0) the result is tpcf_normalize's.  R_0(k1, k2) = 0
+ * gives 0; a singular system gives NaN entries.  Errors: INVALID_ARG for NULL,
+ * nbins or m_max out of range (m_max <= TPCF_MAX_M), scale not > 0.
+ */
+tpcf_status tpcf_edge_correct(const double* d_sums, const double* d_rsums, double scale, int32_t nbins,
+                              int32_t m_max, double* d_zeta, void* stream);
+
 /* Number of points (pixels) of the plan; -1 if plan is NULL. */
 int64_t tpcf_plan_npoints(tpcf_plan plan);
 
@@ -136,6 +171,26 @@ int64_t tpcf_plan_kernel_launches(tpcf_plan plan);
 tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const float* d_w,
                          int64_t pivot_begin, int64_t pivot_end, double* d_zeta, double* d_norm,
                          double* d_sums, void* stream);
+
+/*
+ * Forward with shared neighbour lists, the fast approximate mode of Sec. 3.2 (pivots
+ * very close to one another share one neighbour list).  Each ring's pixels are cut into
+ * runs of `group` consecutive pixels (the last run of a ring shorter), and every pivot
+ * of a run takes the moments of the run's middle pixel rho, neighbours and angles both:
+ *   S_m(k1,k2) = sum_i w_i d_i a_m^{k1}(rho(i)) conj(a_m^{k2}(rho(i))),
+ *   D(k1,k2)   = sum_i w_i W^{k1}(rho(i)) W^{k2}(rho(i)),   zeta = S / D,
+ * over the pivots in [pivot_begin, pivot_end); the moments of rho (eq. Xm.binned) take
+ * every other pixel in the bins, the run's own members included.  The pair work drops
+ * by about `group`; the pivots move by at most (group - 1) / 2 ring pixels.  group = 1
+ * is tpcf_forward.  Map plans without TPCF_CONTRACT_TC, TPCF_SELF_PAIRS_SUBTRACT or a
+ * per-pivot normalisation (else UNSUPPORTED); 1 <= group <= 4096 (else INVALID_ARG).
+ * A call with a new group size builds that tile list (host to device copy, a few MB at
+ * most) and synchronises `stream`; the plan keeps the list of the last group size.
+ * Outputs as tpcf_forward.
+ */
+tpcf_status tpcf_forward_grouped(tpcf_plan plan, const float* d_delta, const float* d_w, int32_t group,
+                                 int64_t pivot_begin, int64_t pivot_end, double* d_zeta, double* d_norm,
+                                 double* d_sums, void* stream);
 
 /*
  * Multi-field forward (end of Sec. 2, after eq. ubEstimator): three fields A, B, C on
@@ -212,7 +267,9 @@ tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_t pivot_beg
  * forward (passes bit 0) and/or the adjoint (bit 1) of the plan on a sample of pivots
  * of the caller's field for every candidate -- register variant sized for 3 or 2
  * resident CTAs per SM, CTAs per SM launched, rings summed in registers between
- * shared-memory flushes -- and keeps the fastest in the plan.  With both passes and
+ * shared-memory flushes, and for the forward the tile layout (32 consecutive pivots,
+ * or four runs of 8 a quarter turn apart whose lanes share the position angles on
+ * rings with another pixel count) -- and keeps the fastest in the plan.  With both passes and
  * the environment variable TPCF_AUTOTUNE_CACHE naming a file, the result is appended
  * there, keyed by device, nside, bins and flags; a later autotune call or
  * tpcf_plan_create_map with the same key takes it from the file without measuring.
@@ -223,11 +280,12 @@ tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_t pivot_beg
  */
 tpcf_status tpcf_plan_autotune(tpcf_plan plan, const float* d_delta, const float* d_w, int32_t passes,
                                void* stream);
-/* The plan's launch configuration: host int32[6] = forward (variant, CTAs per SM,
- * flush rings), adjoint (variant, CTAs per SM, flush rings). */
-tpcf_status tpcf_plan_launch_config(tpcf_plan plan, int32_t* config6);
+/* The plan's launch configuration: host int32[7] = forward (variant, CTAs per SM,
+ * flush rings, tile layout: 0 consecutive pivots, 1 quarter-turn runs), adjoint
+ * (variant, CTAs per SM, flush rings). */
+tpcf_status tpcf_plan_launch_config(tpcf_plan plan, int32_t* config7);
 /* Sets it (same layout); TPCF_ERR_INVALID_ARG for a configuration that does not fit. */
-tpcf_status tpcf_plan_set_launch_config(tpcf_plan plan, const int32_t* config6);
+tpcf_status tpcf_plan_set_launch_config(tpcf_plan plan, const int32_t* config7);
 
 /*
  * Halo of a pixel range, for splitting the adjoint across devices (map plans): the

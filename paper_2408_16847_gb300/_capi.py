@@ -16,6 +16,8 @@ STATUS = {0: "TPCF_OK", 1: "TPCF_ERR_INVALID_ARG", 2: "TPCF_ERR_CUDA", 3: "TPCF_
           4: "TPCF_ERR_TIMEOUT", 5: "TPCF_ERR_UNSUPPORTED", 6: "TPCF_ERR_DEVICE"}
 SELF_PAIRS_SUBTRACT = 1
 CONTRACT_TC = 2
+NORM_BIN_MEAN = 4
+NORM_PIVOT_TOTAL = 8
 MAX_BINS = 32
 MAX_M = 16
 
@@ -25,7 +27,7 @@ EXPORTS = ["tpcf_status_string", "tpcf_last_error", "tpcf_plan_create_map", "tpc
            "tpcf_batch_launch", "tpcf_batch_kernel_launches", "tpcf_batch_destroy", "tpcf_forward_batched", "tpcf_plan_sync", "tpcf_normalize",
            "tpcf_plan_destroy", "tpcf_test_fail_allocation", "tpcf_test_live_allocations",
            "tpcf_plan_halo", "tpcf_plan_autotune", "tpcf_plan_launch_config", "tpcf_plan_set_launch_config",
-           "tpcf_probe_fp32_peak", "tpcf_forward_multi"]
+           "tpcf_probe_fp32_peak", "tpcf_forward_multi", "tpcf_edge_correct", "tpcf_forward_grouped"]
 
 
 class TpcfError(RuntimeError):
@@ -67,6 +69,8 @@ def lib() -> ctypes.CDLL:
     L.tpcf_plan_kernel_launches.argtypes = [_vp]
     L.tpcf_forward.restype = ctypes.c_int
     L.tpcf_forward.argtypes = [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]
+    L.tpcf_forward_grouped.restype = ctypes.c_int
+    L.tpcf_forward_grouped.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _i64, _i64, _vp, _vp, _vp, _vp]
     L.tpcf_forward_noalloc.restype = ctypes.c_int
     L.tpcf_forward_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]
     L.tpcf_backward.restype = ctypes.c_int
@@ -89,6 +93,8 @@ def lib() -> ctypes.CDLL:
     L.tpcf_forward_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32] + [ctypes.POINTER(_vp)] * 6 + [_vp]
     L.tpcf_normalize.restype = ctypes.c_int
     L.tpcf_normalize.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+    L.tpcf_edge_correct.restype = ctypes.c_int
+    L.tpcf_edge_correct.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     L.tpcf_plan_sync.restype = ctypes.c_int
     L.tpcf_plan_sync.argtypes = [_vp]
     L.tpcf_plan_destroy.restype = None

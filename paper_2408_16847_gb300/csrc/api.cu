@@ -152,12 +152,23 @@ static tpcf_status check_bins(const tpcf_bins* b) {
     if (!b || !b->theta_edges_rad) return TPCF_ERR_INVALID_ARG;
     if (b->nbins < 1 || b->nbins > TPCF_MAX_BINS) return TPCF_ERR_INVALID_ARG;
     if (b->m_max < 0 || b->m_max > TPCF_MAX_M) return TPCF_ERR_INVALID_ARG;
-    if (b->flags & ~(uint32_t)(TPCF_SELF_PAIRS_SUBTRACT | TPCF_CONTRACT_TC)) return TPCF_ERR_INVALID_ARG;
+    if (b->flags & ~(uint32_t)(TPCF_SELF_PAIRS_SUBTRACT | TPCF_CONTRACT_TC | NORM_FLAGS)) return TPCF_ERR_INVALID_ARG;
+    if ((b->flags & NORM_FLAGS) == NORM_FLAGS) return TPCF_ERR_INVALID_ARG;
     const double* t = b->theta_edges_rad;
     if (!(t[0] > 0.0)) return TPCF_ERR_INVALID_ARG;
     for (int e = 0; e < b->nbins; ++e)
         if (!(t[e + 1] > t[e])) return TPCF_ERR_INVALID_ARG;
     if (!(t[b->nbins] < 0.5 * M_PI)) return TPCF_ERR_INVALID_ARG;
+    return TPCF_OK;
+}
+
+// Flag combinations the kernels do not implement: a per-pivot normalisation with
+// self-pair subtraction or the tensor-core contraction.
+static tpcf_status check_norm(const tpcf_bins* b) {
+    if ((b->flags & NORM_FLAGS) && (b->flags & (TPCF_SELF_PAIRS_SUBTRACT | TPCF_CONTRACT_TC))) {
+        set_error("per-pivot normalisation with self-pair subtraction or the TC contraction");
+        return TPCF_ERR_UNSUPPORTED;
+    }
     return TPCF_OK;
 }
 
@@ -279,6 +290,7 @@ extern "C" tpcf_status tpcf_plan_create_map(tpcf_plan* out, int64_t nside, const
     *out = nullptr;
     if (nside < 1 || nside > 8192) return TPCF_ERR_INVALID_ARG;
     tpcf_status st = check_bins(bins);
+    if (st == TPCF_OK) st = check_norm(bins);
     if (st != TPCF_OK) return st;
     tpcf_plan_s* P = new (std::nothrow) tpcf_plan_s();
     if (!P) return TPCF_ERR_OOM;
@@ -320,6 +332,7 @@ extern "C" tpcf_status tpcf_plan_create_catalog(tpcf_plan* out, const double* d_
         set_error("catalogue plans use the FP32 contraction");
         return TPCF_ERR_UNSUPPORTED;
     }
+    if (st == TPCF_OK) st = check_norm(bins);
     if (st != TPCF_OK) return st;
     tpcf_plan_s* P = new (std::nothrow) tpcf_plan_s();
     if (!P) return TPCF_ERR_OOM;
@@ -375,13 +388,21 @@ static int64_t ring_first_pixel(int64_t nside, int64_t ri) {  // 0-based ring
 
 // Tiles [*tlo, *thi) that hold the pivots [lo, hi) (tiles are 32 consecutive pixels
 // of one ring, rings in order).
-static void tile_range(const tpcf_plan_s* P, int64_t lo, int64_t hi, int64_t* tlo, int64_t* thi) {
+// Tiles [tlo, thi) that can hold a pivot of [lo, hi).  Linear layout: the tiles of the
+// range's pixels.  Quadrant layout (the forward kernels): a partial ring's pivots are
+// spread over all of its tiles, so whole rings at the two ends.
+static void tile_range(const tpcf_plan_s* P, int64_t lo, int64_t hi, int64_t* tlo, int64_t* thi, bool quad) {
     if (hi <= lo) {
         *tlo = *thi = 0;
         return;
     }
     const int64_t nside = P->map.nside;
     const int64_t ra = ring_of_pixel(nside, lo), rb = ring_of_pixel(nside, hi - 1);
+    if (quad) {
+        *tlo = P->tile_off_h[ra];
+        *thi = rb + 1 < (int64_t)P->tile_off_h.size() ? P->tile_off_h[rb + 1] : P->map.ntiles;
+        return;
+    }
     *tlo = P->tile_off_h[ra] + (lo - ring_first_pixel(nside, ra)) / TILE;
     *thi = P->tile_off_h[rb] + (hi - 1 - ring_first_pixel(nside, rb)) / TILE + 1;
 }
@@ -391,8 +412,9 @@ static int launch_grid(const tpcf_plan_s* P, const tpcf_plan_s::Tune& t, int64_t
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
 }
 
+// group > 1: shared neighbour lists over P->gtiles (tpcf_forward_grouped).
 static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
-                               double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s) {
+                               double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s, int group = 1) {
     const MapDev& g = P->map;
     pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(d_delta, d_w, P->wdw, g.npix);
     P->launches += 4;  // pack, forward, reduce, finalize
@@ -406,8 +428,17 @@ static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float
     c.counter = P->counter;
     c.status = P->status;
     c.self_subtract = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
+    c.norm = norm_of_flags(P->flags);
     c.flush = P->tune_fwd.flush;
-    tile_range(P, lo, hi, &c.tile_lo, &c.tile_hi);
+    if (group > 1) {  // every run tile; those without a pivot in range return at once
+        c.group = group;
+        c.gtiles = P->gtiles;
+        c.tile_lo = 0;
+        c.tile_hi = P->ngtiles;
+    } else {
+        c.quad = P->tune_fwd.quad;
+        tile_range(P, lo, hi, &c.tile_lo, &c.tile_hi, c.quad != 0);
+    }
     const int grid = launch_grid(P, P->tune_fwd, c.tile_hi - c.tile_lo, P->fwd_grid);
     if (P->flags & TPCF_CONTRACT_TC)
         TRY_CUDA(kLaunch[P->M].fwd_tc(g, c, grid, s));
@@ -419,6 +450,43 @@ static tpcf_status map_forward(tpcf_plan_s* P, const float* d_delta, const float
                                                         d_norm, d_sums);
     TRY_CUDA(cudaGetLastError());
     return TPCF_OK;
+}
+
+extern "C" tpcf_status tpcf_forward_grouped(tpcf_plan plan, const float* d_delta, const float* d_w, int32_t group,
+                                            int64_t pivot_begin, int64_t pivot_end, double* d_zeta, double* d_norm,
+                                            double* d_sums, void* stream) {
+    if (!plan || !d_delta || !d_w || !d_zeta || !d_norm) return TPCF_ERR_INVALID_ARG;
+    if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
+    if (group < 1 || group > 4096) return TPCF_ERR_INVALID_ARG;
+    if (plan->kind != PLAN_MAP || (plan->flags & (TPCF_CONTRACT_TC | TPCF_SELF_PAIRS_SUBTRACT | NORM_FLAGS))) {
+        set_error("tpcf_forward_grouped: map plans with the default flags only");
+        return TPCF_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    if (group == 1) return map_forward(plan, d_delta, d_w, pivot_begin, pivot_end, d_zeta, d_norm, d_sums, s);
+    tpcf_plan_s* P = plan;
+    if (P->ggroup != group) {  // the tile list of this run length: ceil(ceil(n_i / group) / 32) per ring
+        const int64_t nside = P->map.nside;
+        std::vector<int2> t;
+        for (int r = 0; r < P->map.nrings; ++r) {
+            const int64_t ri = r + 1;
+            const int64_t n = ri < nside ? 4 * ri : (ri <= 3 * nside ? 4 * nside : 4 * (4 * nside - ri));
+            const int64_t ng = (n + group - 1) / group;
+            for (int64_t f = 0; f < ng; f += TILE) t.push_back(make_int2(r, (int)f));
+        }
+        if ((int64_t)t.size() > P->gtiles_cap) {
+            int2* buf = nullptr;
+            TRY_CUDA(P->alloc(&buf, t.size()));
+            P->gtiles = buf;
+            P->gtiles_cap = (int64_t)t.size();
+        }
+        TRY_CUDA(cudaMemcpyAsync(P->gtiles, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        P->ngtiles = (int64_t)t.size();
+        P->ggroup = group;
+    }
+    return map_forward(P, d_delta, d_w, pivot_begin, pivot_end, d_zeta, d_norm, d_sums, s, group);
 }
 
 extern "C" tpcf_status tpcf_forward(tpcf_plan plan, const float* d_delta, const float* d_w, int64_t pivot_begin,
@@ -443,7 +511,7 @@ extern "C" tpcf_status tpcf_forward_multi(tpcf_plan plan, const float* d_delta_a
         return TPCF_ERR_INVALID_ARG;
     if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
     tpcf_plan_s* P = plan;
-    if (P->kind != PLAN_MAP || (P->flags & (TPCF_CONTRACT_TC | TPCF_SELF_PAIRS_SUBTRACT))) {
+    if (P->kind != PLAN_MAP || (P->flags & (TPCF_CONTRACT_TC | TPCF_SELF_PAIRS_SUBTRACT | NORM_FLAGS))) {
         set_error("tpcf_forward_multi: map plans with the FP32 contraction, self pairs kept");
         return TPCF_ERR_UNSUPPORTED;
     }
@@ -485,7 +553,7 @@ extern "C" tpcf_status tpcf_forward_multi(tpcf_plan plan, const float* d_delta_a
     c.counter = P->counter;
     c.status = P->status;
     c.flush = P->tune_fwd.flush;
-    tile_range(P, pivot_begin, pivot_end, &c.tile_lo, &c.tile_hi);
+    tile_range(P, pivot_begin, pivot_end, &c.tile_lo, &c.tile_hi, true);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.tile_hi - c.tile_lo, P->multi_grid));
     TRY_CUDA(kMulti[M](g, c, P->wdw_b, P->wdw_c, grid, s));
     reduce_slots_kernel<<<n_blocks(nent, 128), 128, 0, s>>>(P->mslots, P->multi_grid, nent, P->msums);
@@ -510,7 +578,7 @@ extern "C" tpcf_status tpcf_count_pairs(tpcf_plan plan, const float* d_w, int64_
     plan->launches += 2;
     TRY_CUDA(cudaMemsetAsync(d_counts, 0, 3 * sizeof(int64_t), s));
     int64_t tlo, thi;
-    tile_range(plan, pivot_begin, pivot_end, &tlo, &thi);
+    tile_range(plan, pivot_begin, pivot_end, &tlo, &thi, false);
     TRY_CUDA(map_count_launch(g, plan->wdw, pivot_begin, pivot_end, tlo, thi, (unsigned long long*)d_counts,
                               plan->num_sms * 4, s));
     return TPCF_OK;
@@ -536,7 +604,7 @@ static tpcf_status map_backward(tpcf_plan_s* P, const float* d_delta, const floa
     c.grad = d_grad;
     c.self_subtract = self;
     c.flush = P->tune_bwd.flush;
-    tile_range(P, lo, hi, &c.tile_lo, &c.tile_hi);
+    tile_range(P, lo, hi, &c.tile_lo, &c.tile_hi, false);
     const int grid = launch_grid(P, P->tune_bwd, c.tile_hi - c.tile_lo, P->bwd_grid);
     TRY_CUDA(kLaunch[P->M].bwd(g, c, grid, P->tune_bwd.variant, s));
     return TPCF_OK;
@@ -547,6 +615,10 @@ extern "C" tpcf_status tpcf_backward(tpcf_plan plan, const float* d_delta, const
                                      float* d_grad, void* stream) {
     if (!plan || !d_delta || !d_w || !d_norm || !d_dL_dzeta || !d_grad) return TPCF_ERR_INVALID_ARG;
     if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
+    if (plan->flags & NORM_FLAGS) {
+        set_error("tpcf_backward: plans with a per-pivot normalisation have no adjoint");
+        return TPCF_ERR_UNSUPPORTED;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     if (plan->kind == PLAN_MAP)

@@ -214,6 +214,7 @@ static tpcf_status batch_build(tpcf_batch_s* B, const tpcf_plan* plans, const fl
             it.c.grad = io[i].grad;
             it.c.self_subtract = io[i].self_subtract;
             it.c.flush = P->tune_fwd.flush;
+            it.c.quad = P->tune_fwd.quad;
             it.c.tile_lo = 0;
             it.c.tile_hi = P->map.ntiles;
             it.tile0 = t0;
@@ -263,6 +264,10 @@ extern "C" tpcf_status tpcf_batch_create(tpcf_batch* out, const tpcf_plan* plans
         if (with_bwd && (!d_dL_dzeta[i] || !d_grad[i])) return TPCF_ERR_INVALID_ARG;
         if (P->flags & TPCF_CONTRACT_TC) {
             set_error("batch members use the FP32 contraction (plan has TPCF_CONTRACT_TC)");
+            return TPCF_ERR_UNSUPPORTED;
+        }
+        if (P->flags & NORM_FLAGS) {
+            set_error("batch members use the default normalisation");
             return TPCF_ERR_UNSUPPORTED;
         }
         if (with_bwd && (P->flags & TPCF_SELF_PAIRS_SUBTRACT)) {

@@ -20,12 +20,15 @@
 namespace tpcf {
 
 constexpr float CAT_AMB = 2.0e-6f;  // relative margin of fp32 chord^2 to an edge (error ~3e-7)
-constexpr double CAT_EPS = 1.0e-7;  // angular margin of the cell query (rad)
+constexpr float CAT_MARGIN = 8.0e-6f;  // angular margin of the fp32 cell query (rad)
 
-// Bin of chord^2 c2 in fp64 over the edges (ties to the upper bin): -1 below the
-// first edge, K at or beyond the last.
+// Bin of chord^2 in fp64 over the edges (ties to the upper bin) for sorted points j
+// (candidate) and si (pivot; si < 0: the placeholder pivot (0, 0, 1) of a padding
+// lane): -1 below the first edge, K at or beyond the last.
 static __device__ __noinline__ int cat_exact_bin(const double* __restrict__ Ed2, int K, const double* __restrict__ xyz,
-                                          int64_t j, double px, double py, double pz) {
+                                          int64_t j, int64_t si) {
+    const double px = si >= 0 ? xyz[3 * si] : 0.0, py = si >= 0 ? xyz[3 * si + 1] : 0.0,
+                 pz = si >= 0 ? xyz[3 * si + 2] : 1.0;
     const double dx = xyz[3 * j] - px, dy = xyz[3 * j + 1] - py, dz = xyz[3 * j + 2] - pz;
     const double c2 = dx * dx + dy * dy + dz * dz;
     int k = -1;
@@ -72,25 +75,29 @@ __host__ __device__ inline size_t cat_tile_bytes(int K) {
     return tile_floats<M>(K) * sizeof(float) + (size_t)NWARPS * TILE * (2 * sizeof(float4) + sizeof(float2));
 }
 
-// The lane's pivot: fp32 hi/lo position, local north / east basis and the FP64
-// position (kept for the rare exact bin decisions).
+// The lane's pivot: fp32 hi/lo position, local north / east basis and its sorted
+// index (the FP64 position is read only for the rare exact bin decisions).
 struct CatPivot {
     float hx, hy, hz, lx, ly, lz;
     float nx, ny, nz, ex, ey;
-    double px, py, pz;
+    int64_t si;
 };
 
-__device__ __forceinline__ CatPivot cat_pivot(double px, double py, double pz) {
+// si < 0: a padding lane, placed at (0, 0, 1).
+__device__ __forceinline__ CatPivot cat_pivot(const CatDev& g, int64_t si) {
     CatPivot P;
-    P.px = px;
-    P.py = py;
-    P.pz = pz;
-    P.hx = (float)px;
-    P.hy = (float)py;
-    P.hz = (float)pz;
-    P.lx = (float)(px - (double)P.hx);
-    P.ly = (float)(py - (double)P.hy);
-    P.lz = (float)(pz - (double)P.hz);
+    P.si = si;
+    float4 h = make_float4(0.0f, 0.0f, 1.0f, 0.0f), l = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (si >= 0) {
+        h = g.p_hi[si];
+        l = g.p_lo[si];
+    }
+    P.hx = h.x;
+    P.hy = h.y;
+    P.hz = h.z;
+    P.lx = l.x;
+    P.ly = l.y;
+    P.lz = l.z;
     // the basis in fp32 (its rounding is a fixed rotation of the pivot's frame, which
     // cancels in a conj(a), plus ~1e-7 of non-orthogonality)
     const float s2 = fmaf(P.hx, P.hx, P.hy * P.hy);
@@ -111,55 +118,65 @@ __device__ __forceinline__ CatPivot cat_pivot(double px, double py, double pz) {
     return P;
 }
 
-// Warp 0: the bounding cap of the tile's live pivots (FP64) into s_cap = (centre,
-// query radius R + theta_max + CAT_EPS).  The caller synchronises afterwards.
-__device__ __forceinline__ void cat_tile_cap(const CatDev& g, bool live, double px, double py, double pz,
-                                             double* s_cap) {
-    double sx = live ? px : 0.0, sy = live ? py : 0.0, sz = live ? pz : 0.0;
+// Warp 0: a cap holding every live pivot of the tile together with its neighbours
+// (radius theta_max), as a range of cell bands and a longitude half-width about the
+// cap's centre: s_cap = (phi_c, dphi, first band, last band, full).  All in fp32:
+// CAT_MARGIN (rad) exceeds every rounding of the centre, radius, colatitude and band
+// division (each below ~1e-6 rad), and the sine ratio is rounded up, so the cells are
+// a superset of the exact cap; bins are then decided per candidate.  The caller
+// synchronises afterwards.
+__device__ __forceinline__ void cat_tile_cap(const CatDev& g, bool live, const CatPivot& P, float* s_cap) {
+    const float px = P.hx + P.lx, py = P.hy + P.ly, pz = P.hz + P.lz;
+    float sx = live ? px : 0.0f, sy = live ? py : 0.0f, sz = live ? pz : 0.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
     }
-    double nrm = sqrt(sx * sx + sy * sy + sz * sz);
-    if (!(nrm > 1e-300)) {  // live pivots cancel out: any centre will do (r is measured from it)
-        sx = 0.0;
-        sy = 0.0;
-        sz = 1.0;
-        nrm = 1.0;
+    float nrm = sqrtf(fmaf(sx, sx, fmaf(sy, sy, sz * sz)));
+    if (!(nrm > 1e-6f)) {  // live pivots cancel out: any centre will do (r is measured from it)
+        sx = 0.0f;
+        sy = 0.0f;
+        sz = 1.0f;
+        nrm = 1.0f;
     }
-    const double cx = sx / nrm, cy = sy / nrm, cz = sz / nrm;
-    double r = 0.0;
+    const float cx = sx / nrm, cy = sy / nrm, cz = sz / nrm;
+    float r = 0.0f;
     if (live) {
-        const double dx = px - cx, dy = py - cy, dz = pz - cz;
-        const double ch = sqrt(dx * dx + dy * dy + dz * dz);
-        r = 2.0 * asin(fmin(1.0, 0.5 * ch));
+        const float dx = px - cx, dy = py - cy, dz = pz - cz;
+        const float ch = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        r = 2.0f * asinf(fminf(1.0f, 0.5f * ch));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
     if ((threadIdx.x & 31) == 0) {
-        // bands within reach and the cap's longitude half-width, valid for every
-        // colatitude it reaches; s_cap = (phi_c, dphi, b0, b1, full)
-        const double Q = r + g.theta_max + CAT_EPS;
-        const double thc = atan2(sqrt(cx * cx + cy * cy), cz);
-        double phc = atan2(cy, cx);
-        if (phc < 0.0) phc += 2.0 * M_PI;
+        const float PI_F = 3.14159265f;
+        const float Q = r + (float)g.theta_max + CAT_MARGIN;
+        const float thc = atan2f(sqrtf(fmaf(cx, cx, cy * cy)), cz);
+        float phc = atan2f(cy, cx);
+        if (phc < 0.0f) phc += 2.0f * PI_F;
         int b0 = 0, b1 = g.nbands - 1;
-        double full = 1.0, dphi = M_PI;
-        if (Q < M_PI) {
-            b0 = max(0, (int)floor((thc - Q) / g.hband));
-            b1 = min(g.nbands - 1, (int)floor((thc + Q) / g.hband));
-            const double sq = sin(Q), st = sin(thc);
-            if (thc - Q > 0.0 && thc + Q < M_PI && sq < st) {
-                full = 0.0;
-                dphi = asin(sq / st) + CAT_EPS;
+        float full = 1.0f, dphi = PI_F;
+        const float lo = thc - Q - CAT_MARGIN, hi = thc + Q + CAT_MARGIN;
+        if (Q < PI_F) {
+            const float hb = (float)g.hband;
+            b0 = max(0, (int)floorf(lo / hb));
+            b1 = min(g.nbands - 1, (int)floorf(hi / hb));
+            if (lo > 0.0f && hi < PI_F) {  // no pole inside: then Q < pi / 2, sin rises with Q
+                // sin is concave on [0, pi]: its least value over thc +- margin is at an end
+                const float st = fminf(sinf(thc - CAT_MARGIN), sinf(thc + CAT_MARGIN));
+                const float x = sinf(Q) / st * (1.0f + 1.0e-6f);
+                if (x < 1.0f) {
+                    full = 0.0f;
+                    dphi = asinf(x) + CAT_MARGIN;
+                }
             }
         }
         s_cap[0] = phc;
         s_cap[1] = dphi;
-        s_cap[2] = (double)b0;
-        s_cap[3] = (double)b1;
+        s_cap[2] = (float)b0;
+        s_cap[3] = (float)b1;
         s_cap[4] = full;
     }
 }
@@ -170,16 +187,16 @@ __device__ __forceinline__ void cat_tile_cap(const CatDev& g, bool live, double 
 // same candidate at the same time).  Candidates are staged 32 at a
 // time in the warp's shared buffers wh / wl / wv.
 template <class F>
-__device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restrict__ wdw, const double* s_cap,
+__device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restrict__ wdw, const float* s_cap,
                                          const CatPivot& P, const float* sE2, const unsigned char* slut,
                                          float4* wh, float4* wl, float2* wv, F&& f) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = g.K;
     // sector bounds in fp32: the extra 4e-6 rad covers its rounding (phi < 2 pi), so the
     // cell ranges stay a superset of the cap
-    const float phc = (float)s_cap[0], dphi = (float)s_cap[1] + 4.0e-6f;
+    const float phc = s_cap[0], dphi = s_cap[1] + 4.0e-6f;
     const int b0 = (int)s_cap[2], b1 = (int)s_cap[3];
-    const bool full = s_cap[4] != 0.0;
+    const bool full = s_cap[4] != 0.0f;
     // every warp walks every band and takes every NWARPS-th chunk of 32 candidates
     int chunk = 0;
     for (int b = b0; b <= b1; ++b) {
@@ -230,7 +247,7 @@ __device__ __forceinline__ void cat_walk(const CatDev& g, const float2* __restri
                     int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
                     const int e1 = max(k, 0), e2 = min(k + 1, K);
                     if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
-                        k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.px, P.py, P.pz);
+                        k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.si);
                     f(k, dx, dy, dz, wv[u], __float_as_int(ql.w));
                 }
             }
@@ -257,14 +274,14 @@ constexpr int CAT_GROUPS = 4;
 
 template <class FP, class FE, class FS, class FC>
 __device__ __forceinline__ void cat_walk_grouped(const CatDev& g, const float2* __restrict__ wdw,
-                                                 const double* s_cap, const CatPivot& P, const float* sE2,
+                                                 const float* s_cap, const CatPivot& P, const float* sE2,
                                                  const unsigned char* slut, float4* wh, float4* wl, float2* wv,
                                                  FP&& pair, FE&& group_end, FS&& single, FC&& chunk_end) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = g.K;
-    const float phc = (float)s_cap[0], dphi = (float)s_cap[1] + 4.0e-6f;
+    const float phc = s_cap[0], dphi = s_cap[1] + 4.0e-6f;
     const int b0 = (int)s_cap[2], b1 = (int)s_cap[3];
-    const bool full = s_cap[4] != 0.0;
+    const bool full = s_cap[4] != 0.0f;
     int chunk = 0;
     for (int b = b0; b <= b1; ++b) {
         const int64_t ns = g.band_ns[b];
@@ -319,7 +336,7 @@ __device__ __forceinline__ void cat_walk_grouped(const CatDev& g, const float2* 
                     int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
                     const int e1 = max(k, 0), e2 = min(k + 1, K);
                     if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
-                        k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.px, P.py, P.pz);
+                        k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.si);
                     if (k < 0 || k >= K) continue;
                     if (kb == -1000) kb = max(k - 1, 0);
                     const int q = k - kb;
@@ -364,7 +381,7 @@ __device__ __forceinline__ void cat_walk_grouped(const CatDev& g, const float2* 
                         int k = cat_bin(c2, sE2, slut, g.lut_l0, g.lut_inv, K);
                         const int e1 = max(k, 0), e2 = min(k + 1, K);
                         if (fabsf(c2 - sE2[e1]) <= CAT_AMB * sE2[e1] || fabsf(c2 - sE2[e2]) <= CAT_AMB * sE2[e2])
-                            k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.px, P.py, P.pz);
+                            k = cat_exact_bin(g.Ed2, K, g.xyz, (int64_t)__float_as_int(ql.w), P.si);
                         single(k, dx, dy, dz, wv[u], u);
                     }
                 }
@@ -378,7 +395,7 @@ template <int M, bool SELF>
 __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall c) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_tile;
-    __shared__ double s_cap[5];  // cap query: phi_c, dphi, first band, last band, full
+    __shared__ float s_cap[5];  // cap query: phi_c, dphi, first band, last band, full
     __shared__ float sE2[TPCF_MAX_BINS + 1];
     __shared__ unsigned char slut[CAT_LUT];
     const int K = g.K;
@@ -404,7 +421,6 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
         const int64_t si = (int64_t)tile * TILE + lane;
         bool live = false;
         float2 pv = make_float2(0.0f, 0.0f);
-        double px = 0.0, py = 0.0, pz = 1.0;
         if (si < g.n) {
             const int64_t o = g.orig[si];
             if (o >= c.piv_lo && o < c.piv_hi) {
@@ -412,9 +428,6 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
                 live = pv.y != 0.0f;
                 if (!live) pv = make_float2(0.0f, 0.0f);
             }
-            px = g.xyz[3 * si];
-            py = g.xyz[3 * si + 1];
-            pz = g.xyz[3 * si + 2];
         }
         if (!__syncthreads_or(live)) continue;
         for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
@@ -422,9 +435,9 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
             sPiv[lane] = pv.x;
             sPiv[TILE + lane] = pv.y;
         }
-        if (warp == 0) cat_tile_cap(g, live, px, py, pz, s_cap);
+        const CatPivot P = cat_pivot(g, si < g.n ? si : -1);
+        if (warp == 0) cat_tile_cap(g, live, P, s_cap);
         __syncthreads();
-        const CatPivot P = cat_pivot(px, py, pz);
 
         float2 acc[M + 1];
 #pragma unroll
@@ -465,6 +478,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
             },
             [&](int64_t, int) {});
         __syncthreads();
+        if (c.norm != NORM_NONE) tile_normalize<M>(K, sA, sW, c.norm);
         tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
         __syncthreads();
     }
@@ -487,7 +501,7 @@ template <int M>
 __global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall c) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_tile;
-    __shared__ double s_cap[5];
+    __shared__ float s_cap[5];
     __shared__ float sE2[TPCF_MAX_BINS + 1];
     __shared__ unsigned char slut[CAT_LUT];
     const int K = g.K;
@@ -514,7 +528,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall 
         const int64_t si = (int64_t)tile * TILE + lane;
         bool live = false;
         float2 pv = make_float2(0.0f, 0.0f);
-        double px = 0.0, py = 0.0, pz = 1.0;
         int64_t oi = -1;
         if (si < g.n) {
             oi = g.orig[si];
@@ -523,9 +536,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall 
                 live = pv.y != 0.0f;
                 if (!live) pv = make_float2(0.0f, 0.0f);
             }
-            px = g.xyz[3 * si];
-            py = g.xyz[3 * si + 1];
-            pz = g.xyz[3 * si + 2];
         }
         if (!__syncthreads_or(live)) continue;
         for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
@@ -534,9 +544,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) cat_bwd_kernel(CatDev g, MapCall 
             sPiv[TILE + lane] = pv.y;
             sPrim[lane] = 0.0f;
         }
-        if (warp == 0) cat_tile_cap(g, live, px, py, pz, s_cap);
+        const CatPivot P = cat_pivot(g, si < g.n ? si : -1);
+        if (warp == 0) cat_tile_cap(g, live, P, s_cap);
         __syncthreads();
-        const CatPivot P = cat_pivot(px, py, pz);
 
         // phase 1: the moments, as in the forward
         {
@@ -667,7 +677,7 @@ __global__ void __launch_bounds__(NTHREADS) cat_count_kernel(CatDev g, const flo
                                                              long long hi, int* counter,
                                                              unsigned long long* counts) {
     __shared__ int s_tile;
-    __shared__ double s_cap[5];
+    __shared__ float s_cap[5];
     __shared__ float sE2[TPCF_MAX_BINS + 1];
     __shared__ unsigned char slut[CAT_LUT];
     __shared__ __align__(16) float4 sCh[NWARPS * TILE];
@@ -684,18 +694,14 @@ __global__ void __launch_bounds__(NTHREADS) cat_count_kernel(CatDev g, const flo
         if ((long long)tile >= g.ntiles) break;
         const int64_t si = (int64_t)tile * TILE + lane;
         bool live = false;
-        double px = 0.0, py = 0.0, pz = 1.0;
         if (si < g.n) {
             const int64_t o = g.orig[si];
             live = o >= lo && o < hi && wdw[si].y != 0.0f;
-            px = g.xyz[3 * si];
-            py = g.xyz[3 * si + 1];
-            pz = g.xyz[3 * si + 2];
         }
         if (!__syncthreads_or(live)) continue;
-        if (warp == 0) cat_tile_cap(g, live, px, py, pz, s_cap);
+        const CatPivot P = cat_pivot(g, si < g.n ? si : -1);
+        if (warp == 0) cat_tile_cap(g, live, P, s_cap);
         __syncthreads();
-        const CatPivot P = cat_pivot(px, py, pz);
         unsigned long long cnt = 0;
         cat_walk(g, wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
                  [&](int k, float, float, float, float2, int) { cnt += (k >= 0 && k < K) ? 1ull : 0ull; });

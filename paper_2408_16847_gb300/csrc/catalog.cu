@@ -141,6 +141,96 @@ __global__ void normalize_kernel(const double* __restrict__ sums, const double* 
     zeta[2 * idx + 1] = d != 0.0 ? sums[2 * idx + 1] / d : 0.0;
 }
 
+// m-coupling correction, one CTA per bin pair (k1, k2): the (2M+1) x (2M+1) system
+//   sum_{m'=-M..M} scale R_{m-m'} z_{m'} = S_m,   m = -M..M,   X_{-n} = conj(X_n),
+// solved by Gaussian elimination with partial pivoting in FP64 shared memory; writes
+// z_m, m = 0..M.  R_0 = 0 gives zeta = 0; a zero pivot gives NaN.
+constexpr int EC_MAX_N = 2 * TPCF_MAX_M + 1;
+constexpr int EC_THREADS = 128;
+
+__device__ __forceinline__ double2 c_ext(const double* X, int K, int k1, int k2, int n) {
+    const double* e = X + 2 * (((size_t)(n < 0 ? -n : n) * K + k1) * K + k2);
+    return n >= 0 ? make_double2(e[0], e[1]) : make_double2(e[0], -e[1]);
+}
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 c_div(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__global__ void __launch_bounds__(EC_THREADS) edge_correct_kernel(const double* __restrict__ S,
+                                                                  const double* __restrict__ R, double scale, int K,
+                                                                  int M, double* __restrict__ zeta) {
+    __shared__ double2 A[EC_MAX_N][EC_MAX_N + 1];  // augmented: column N holds the right-hand side
+    __shared__ int s_piv;
+    const int k1 = blockIdx.x / K, k2 = blockIdx.x % K;
+    const int N = 2 * M + 1;
+    double* out = zeta + 2 * ((size_t)k1 * K + k2);
+    const size_t mstride = 2 * (size_t)K * K;
+    const double2 r0 = c_ext(R, K, k1, k2, 0);
+    if (r0.x == 0.0 && r0.y == 0.0) {
+        for (int m = threadIdx.x; m <= M; m += EC_THREADS) out[m * mstride] = out[m * mstride + 1] = 0.0;
+        return;
+    }
+    for (int e = threadIdx.x; e < N * (N + 1); e += EC_THREADS) {
+        const int r = e / (N + 1), c = e % (N + 1);
+        if (c < N) {
+            const double2 v = c_ext(R, K, k1, k2, r - c);
+            A[r][c] = make_double2(scale * v.x, scale * v.y);
+        } else {
+            A[r][c] = c_ext(S, K, k1, k2, r - M);
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < N; ++j) {
+        if (threadIdx.x == 0) {
+            int best = j;
+            double bv = A[j][j].x * A[j][j].x + A[j][j].y * A[j][j].y;
+            for (int r = j + 1; r < N; ++r) {
+                const double v = A[r][j].x * A[r][j].x + A[r][j].y * A[r][j].y;
+                if (v > bv) bv = v, best = r;
+            }
+            s_piv = best;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != j)
+            for (int c = j + threadIdx.x; c <= N; c += EC_THREADS) {
+                const double2 t = A[j][c];
+                A[j][c] = A[p][c];
+                A[p][c] = t;
+            }
+        __syncthreads();
+        const double2 piv = A[j][j];
+        const int rows = N - j - 1, cols = N - j;  // rows below j, columns j+1..N
+        for (int e = threadIdx.x; e < rows * cols; e += EC_THREADS) {
+            const int r = j + 1 + e / cols, c = j + 1 + e % cols;
+            const double2 f = c_div(A[r][j], piv);
+            const double2 t = c_mul(f, A[j][c]);
+            A[r][c] = make_double2(A[r][c].x - t.x, A[r][c].y - t.y);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {  // back substitution into column N
+        for (int r = N - 1; r >= 0; --r) {
+            double2 acc = A[r][N];
+            for (int c = r + 1; c < N; ++c) {
+                const double2 t = c_mul(A[r][c], A[c][N]);
+                acc = make_double2(acc.x - t.x, acc.y - t.y);
+            }
+            const double2 d = A[r][r];
+            A[r][N] = (d.x == 0.0 && d.y == 0.0) ? make_double2(nan(""), nan("")) : c_div(acc, d);
+        }
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m <= M; m += EC_THREADS) {
+        out[m * mstride] = A[M + m][N].x;
+        out[m * mstride + 1] = A[M + m][N].y;
+    }
+}
+
 static int nblk(int64_t n, int bs) { return (int)std::min<int64_t>((n + bs - 1) / bs, 1 << 20); }
 
 tpcf_status build_catalog(tpcf_plan_s* P, const double* d_xyz, int64_t n, cudaStream_t s) {
@@ -306,6 +396,7 @@ tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d
     c.counter = P->counter;
     c.status = P->status;
     c.self_subtract = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
+    c.norm = norm_of_flags(P->flags);
     TRY_CUDA(kCat[P->M].fwd(g, c, P->fwd_grid, s));
     reduce_slots_kernel<<<(P->nent + 127) / 128, 128, 0, s>>>(P->slots, P->fwd_grid, P->nent, P->sums);
     const int nout = (P->M + 1) * P->K * P->K;
@@ -316,6 +407,17 @@ tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d
 }
 
 }  // namespace tpcf
+
+extern "C" tpcf_status tpcf_edge_correct(const double* d_sums, const double* d_rsums, double scale, int32_t nbins,
+                                         int32_t m_max, double* d_zeta, void* stream) {
+    if (!d_sums || !d_rsums || !d_zeta) return TPCF_ERR_INVALID_ARG;
+    if (nbins < 1 || nbins > TPCF_MAX_BINS || m_max < 0 || m_max > TPCF_MAX_M) return TPCF_ERR_INVALID_ARG;
+    if (!(scale > 0.0) || !isfinite(scale)) return TPCF_ERR_INVALID_ARG;
+    tpcf::edge_correct_kernel<<<nbins * nbins, tpcf::EC_THREADS, 0, (cudaStream_t)stream>>>(d_sums, d_rsums, scale,
+                                                                                            nbins, m_max, d_zeta);
+    TRY_CUDA(cudaGetLastError());
+    return TPCF_OK;
+}
 
 extern "C" tpcf_status tpcf_normalize(const double* d_sums, const double* d_norm, double scale, int32_t nbins,
                                       int32_t m_max, double* d_zeta, void* stream) {

@@ -99,10 +99,33 @@ cudaError_t TPCF_CAT(map_fwd_tc_launch_m, TPCF_M)(const MapDev& g, const MapCall
     return cudaGetLastError();
 }
 
+// Resident CTAs per SM from the SM's register file and shared memory.  Used for the
+// tensor-core kernel, for which cudaOccupancyMaxActiveBlocksPerMultiprocessor answers 1
+// although 3 CTAs fit by registers and shared memory (and the profiler's occupancy
+// limits agree); the CTAs are persistent and never wait on each other, so a grid
+// larger than what is resident is still correct.
+template <class Kern>
+static int occupancy_by_resources(Kern* k, size_t smem) {
+    if (prefer_shared(k, smem) != cudaSuccess) return 0;
+    cudaFuncAttributes a;
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+    if (cudaFuncGetAttributes(&a, k) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
+        return 0;
+    const size_t per_cta_smem = smem + a.sharedSizeBytes + (size_t)reserved;
+    const int warps = NTHREADS / 32;
+    const int regs_warp = (a.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+    const int by_smem = (int)((size_t)smem_sm / per_cta_smem);
+    const int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * warps) : 0;
+    return by_smem < by_regs ? by_smem : by_regs;
+}
+
 int TPCF_CAT(map_fwd_tc_occupancy_m, TPCF_M)(int K, int self_subtract) {
     const size_t smem = tc_smem_bytes(K, TPCF_M, self_subtract != 0);
-    const int nb = self_subtract ? occupancy(map_fwd_tc_kernel<TPCF_M, true>, smem)
-                                 : occupancy(map_fwd_tc_kernel<TPCF_M, false>, smem);
+    const int nb = self_subtract ? occupancy_by_resources(map_fwd_tc_kernel<TPCF_M, true>, smem)
+                                 : occupancy_by_resources(map_fwd_tc_kernel<TPCF_M, false>, smem);
     // at most 512 / TC_TMEM_COLS accumulators per SM; more resident CTAs would wait in tcgen05.alloc
     return nb < 512 / TC_TMEM_COLS ? nb : 512 / TC_TMEM_COLS;
 }

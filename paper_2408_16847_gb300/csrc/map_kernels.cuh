@@ -36,6 +36,28 @@ constexpr float AMBIGUITY = 1.0e-6f;  // > worst fp32 error of the edge position
 constexpr float FAST_XMAX = 0.25f;    // |half longitude offset| covered by the polynomial
 constexpr int FLUSH_RINGS = 8;        // default rings summed in registers before a shared-memory flush
 
+// Fire-and-forget FP64 reduction of an fp32 partial sum into a CTA slot.  The float
+// is widened by moving its IEEE 754 fields (exponent re-biased by 1023 - 127 = 896,
+// mantissa shifted up by 52 - 23 = 29 bits), an exact conversion on the integer pipe:
+// the FP64 pipe of this part runs at a few percent of the FP32 rate, and one
+// conversion per slot entry and tile kept it half busy on small tiles.  Zeros add
+// nothing and are skipped; subnormal, infinite and NaN values take the ordinary
+// conversion.
+__device__ __forceinline__ void red_add_f32(double* p, float x) {
+    const unsigned u = __float_as_uint(x);
+    if ((u & 0x7fffffffu) == 0u) return;
+    const unsigned e = (u >> 23) & 0xffu;
+    double d;
+    if (e == 0u || e == 0xffu) {
+        d = (double)x;
+    } else {
+        d = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                             ((unsigned long long)(e + 896u) << 52) |
+                                             ((unsigned long long)(u & 0x7fffffu) << 29)));
+    }
+    atomicAdd(p, d);  // result unused: a reduction, no wait
+}
+
 __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
     long long q = a / b;
     if ((a % b) != 0 && a < 0) --q;
@@ -357,6 +379,67 @@ __device__ __forceinline__ void walk_run(const RingCtx& R, const L& ld, const La
     }
 }
 
+// walk_run for a tile in the quadrant layout (tile_pivot): the four lanes l, l + 8,
+// l + 16, l + 24 hold pivots a quarter turn apart, and since every ring has a multiple
+// of four pixels they see ring r at the same fractional offset, with runs of the same
+// length at the same offset from their own pivot, hence the same position angle at
+// every step.  Each lane of a group computes the (folded) angle of one of every four
+// steps and the group shares them by shuffles; every lane still sums its own pixels.
+// The caller has checked runs_quad().
+template <int M, bool FAST, bool SELF, class L>
+__device__ __forceinline__ void walk_run_quad(const RingCtx& R, const L& ld, const LaneC& c, int a, int len,
+                                              float2 (&acc)[M + 1], float& W, float& Q, float& QW, int mr = M) {
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    if (maxlen <= 0) return;
+    const int lane = threadIdx.x & 31, j = lane >> 3, gb = lane & 7;
+    const float i0 = (float)(a - c.cint);
+    const float xneg = -c.cfrac * R.step, uneg = -c.cfrac * R.inv_n;
+    const int last = max(len - 1, 0);
+    int idx = wrap_idx(a, R.n);
+    const auto row = ld.row(R.first);
+    for (int t0 = 0; t0 < maxlen; t0 += 4) {
+        Fold mine;
+        {
+            // steps past the run take its last offset, a valid direction (zero weight)
+            const int tj = min(t0 + j, last);
+            float cph, sph;
+            pixel_dir<FAST>(i0 + (float)tj, xneg, uneg, R, cph, sph);
+            mine = fold_angle(cph, sph);
+        }
+        // two steps at a time, so that only two shared angles are live
+#pragma unroll
+        for (int h = 0; h < 4; h += 2) {
+            const Fold fa = shfl_fold(mine, gb + 8 * h), fb = shfl_fold(mine, gb + 8 * h + 8);
+            const int i1 = idx + 1 >= R.n ? idx + 1 - R.n : idx + 1;
+            // (the index test is a guard: a run's indices always lie within the ring)
+            const bool ia = t0 + h < len && (unsigned)idx < (unsigned)R.n;
+            const bool ib = t0 + h + 1 < len && (unsigned)i1 < (unsigned)R.n;
+            const float2 va = ia ? row(idx) : make_float2(0.0f, 0.0f);
+            const float2 vb = ib ? row(i1) : make_float2(0.0f, 0.0f);
+            harmonics2f<M>(acc, fa, va.x, va.x, fb, vb.x, vb.x, mr);
+            W += va.y + vb.y;
+            if (SELF) {
+                Q = fmaf(va.x, va.x, fmaf(vb.x, vb.x, Q));
+                QW = fmaf(va.y, va.y, fmaf(vb.y, vb.y, QW));
+            }
+            idx = i1 + 1 >= R.n ? i1 + 1 - R.n : i1 + 1;
+        }
+    }
+}
+
+// True when each lane's run has the same offset from its pivot, the same length and
+// the same fractional pivot position as the other three lanes of its quadrant group
+// (an empty run matches any other empty run).  Every lane takes part in every shuffle.
+__device__ __forceinline__ bool runs_quad(const LaneC& c, int a, int len) {
+    const int gb = threadIdx.x & 7;
+    const int rel = len > 0 ? a - c.cint : 0;
+    const unsigned cf = __float_as_uint(c.cfrac);
+    const int rel0 = __shfl_sync(0xffffffffu, rel, gb);
+    const int len0 = __shfl_sync(0xffffffffu, len, gb);
+    const unsigned cf0 = __shfl_sync(0xffffffffu, cf, gb);
+    return __all_sync(0xffffffffu, rel == rel0 && len == len0 && cf == cf0);
+}
+
 // Walk the pixel pairs (p, mb - p), p in [a, a + len): mirror images about the
 // pivot's meridian (belt rings with as many pixels as the pivot ring).  Two pairs
 // (four pixels) per iteration; the same no-wrap fast loop as walk_run.
@@ -588,7 +671,7 @@ __device__ __forceinline__ ExactCtx exact_ctx(const MapDev& g, const PivotRing& 
 template <int M, bool SELF, class L>
 __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P, int r, int k, int q,
                                              const L& ld, float2 (&acc)[M + 1], float& W,
-                                             float& Q, float& QW, int mr = M) {
+                                             float& Q, float& QW, int mr = M, bool quad = false) {
     const long long pr = P.pair0 + (r - P.rlo);
     const int2 Tk = g.pair_T[pr * (g.K + 1) + k];
     const int2 Tk1 = g.pair_T[pr * (g.K + 1) + k + 1];
@@ -623,6 +706,16 @@ __device__ __forceinline__ void fwd_ring_bin(const MapDev& g, const PivotRing& P
     }
     const float om = fmaxf(run_omax(c, b.a0, b.n0), run_omax(c, b.a1, b.n1));
     const bool fast = __all_sync(0xffffffffu, om * R.step <= FAST_XMAX);
+    if (quad && runs_quad(c, b.a0, b.n0) && runs_quad(c, b.a1, b.n1)) {
+        if (fast) {
+            walk_run_quad<M, true, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW, mr);
+            walk_run_quad<M, true, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW, mr);
+        } else {
+            walk_run_quad<M, false, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW, mr);
+            walk_run_quad<M, false, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW, mr);
+        }
+        return;
+    }
     if (fast) {
         walk_run<M, true, SELF>(R, ld, c, b.a0, b.n0, acc, W, Q, QW, mr);
         walk_run<M, true, SELF>(R, ld, c, b.a1, b.n1, acc, W, Q, QW, mr);
@@ -654,6 +747,33 @@ __device__ __forceinline__ PivotRing pivot_ring(const MapDev& g, int i) {
     return P;
 }
 
+// Pivot of a lane in tile (ring i, start = 32 j).  Linear layout: q = start + lane.
+// Quadrant layout (the forward kernels): q = 8 j + (lane & 7) + (lane >> 3) n_i / 4,
+// four groups of eight consecutive pivots a quarter turn apart (walk_run_quad); a ring
+// has ceil(n_i / 32) tiles either way.  `valid`: q is a pixel of the ring; lanes past
+// the end take the geometry qg of the last pivot (of their quadrant), which keeps every
+// unwrapped pixel index within [-n_r, 2 n_r).
+struct TilePivot {
+    int q, qg;
+    bool valid;
+};
+
+__device__ __forceinline__ TilePivot tile_pivot(int start, int n_i, bool quad) {
+    const int lane = threadIdx.x & 31;
+    TilePivot t;
+    if (quad) {
+        const int quarter = n_i >> 2, qq = (start >> 2) + (lane & 7), off = (lane >> 3) * quarter;
+        t.valid = qq < quarter;
+        t.q = qq + off;
+        t.qg = min(qq, quarter - 1) + off;
+    } else {
+        t.q = start + lane;
+        t.valid = t.q < n_i;
+        t.qg = min(t.q, n_i - 1);
+    }
+    return t;
+}
+
 // Where the tile's moments live in shared memory.  LayKM: A[k][m][re/im][32 pivots],
 // W[k][32], Q[k][32], QW[k][32] (the FP32 contraction and the adjoint read this).
 struct LayKM {
@@ -671,7 +791,7 @@ struct LayKM {
 // Smem must be zeroed beforehand; it is complete after the caller's __syncthreads().
 template <int M, bool SELF, class L, class Lay>
 __device__ __forceinline__ void tile_moments_l(const MapDev& g, const PivotRing& P, int q, const L& ld,
-                                               const Lay& lay, int flush, int mr = M) {
+                                               const Lay& lay, int flush, int mr = M, bool quad = false) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < g.K; ++k) {
         const int2 br = g.bin_range[(long long)P.i * g.K + k];
@@ -685,7 +805,7 @@ __device__ __forceinline__ void tile_moments_l(const MapDev& g, const PivotRing&
         // sums short.
         int nr = 0;
         for (int r = br.x + warp; r <= br.y; r += NWARPS) {
-            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, acc, W, Q, QW, mr);
+            fwd_ring_bin<M, SELF>(g, P, r, k, q, ld, acc, W, Q, QW, mr, quad);
             if (++nr == flush || r + NWARPS > br.y) {
                 nr = 0;
 #pragma unroll
@@ -710,8 +830,47 @@ __device__ __forceinline__ void tile_moments_l(const MapDev& g, const PivotRing&
 
 template <int M, bool SELF, class L>
 __device__ __forceinline__ void tile_moments(const MapDev& g, const PivotRing& P, int q, const L& ld, float* sA,
-                                             float* sW, float* sQ, float* sQW, int flush, int mr = M) {
-    tile_moments_l<M, SELF>(g, P, q, ld, LayKM{sA, sW, sQ, sQW, mr + 1}, flush, mr);
+                                             float* sW, float* sQ, float* sQW, int flush, int mr = M,
+                                             bool quad = false) {
+    tile_moments_l<M, SELF>(g, P, q, ld, LayKM{sA, sW, sQ, sQW, mr + 1}, flush, mr, quad);
+}
+
+// Per-pivot normalisation of the tile's moments (Sec. 3.1): each lane's a_m^k is
+// divided by its bin weight W^k (NORM_BIN_MEAN) or by its total sum_k W^k
+// (NORM_PIVOT_TOTAL), 0 where that weight is 0; W^k is then set to 1, so that the
+// contraction's D entries become the tile's sum of pivot weights.  Layout of
+// tile_moments (m-major within each bin, TILE lanes innermost).  Called by every
+// thread of the CTA after the moments are complete (contains barriers).
+template <int M>
+__device__ __forceinline__ void tile_normalize(int K, float* sA, float* sW, int norm, int mr = M) {
+    constexpr int PER = (TPCF_MAX_BINS * TILE + NTHREADS - 1) / NTHREADS;
+    float inv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * NTHREADS;
+        float W = 0.0f;
+        if (e < K * TILE) {
+            if (norm == NORM_BIN_MEAN) {
+                W = sW[e];
+            } else {
+                const int l = e & (TILE - 1);
+                for (int k = 0; k < K; ++k) W += sW[k * TILE + l];
+            }
+        }
+        inv[u] = W > 0.0f ? 1.0f / W : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * NTHREADS;
+        if (e < K * TILE) {
+            const int k = e / TILE, l = e & (TILE - 1);
+            float* a = sA + (size_t)k * (mr + 1) * 2 * TILE + l;
+            for (int j = 0; j < 2 * (mr + 1); ++j) a[j * TILE] *= inv[u];
+            sW[e] = 1.0f;
+        }
+    }
+    __syncthreads();
 }
 
 // Per-tile partial sums into the CTA's FP64 slot (eq. zetamEst2 summed over the
@@ -746,8 +905,8 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
                 sr = fmaf(wd[l], fmaf(a, cc, b * d), sr);
                 si = fmaf(wd[l], fmaf(a, d, -b * cc), si);
             }
-            atomicAdd(slot + 2 * e, (double)sr);  // no return value: a reduction, no wait
-            atomicAdd(slot + 2 * e + 1, (double)si);
+            red_add_f32(slot + 2 * e, sr);
+            red_add_f32(slot + 2 * e + 1, si);
         } else if (e < nS + P) {
             const int pidx = e - nS;
             int k2 = (int)((sqrtf(8.0f * pidx + 1.0f) - 1.0f) * 0.5f);
@@ -760,7 +919,7 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
                 const int l = (j + threadIdx.x) & (TILE - 1);
                 s = fmaf(wt[l], sW[k1 * TILE + l] * sW[k2 * TILE + l], s);
             }
-            atomicAdd(slot + nS + e, (double)s);
+            red_add_f32(slot + nS + e, s);
         } else {
             const int k = e - nS - P;
             float s1 = 0.0f, s2 = 0.0f;
@@ -769,8 +928,8 @@ __device__ __forceinline__ void tile_contract(int K, const float* sA, const floa
                 s1 = fmaf(wd[l], sQ[k * TILE + l], s1);
                 s2 = fmaf(wt[l], sQW[k * TILE + l], s2);
             }
-            atomicAdd(slot + 2 * nS + P + k, (double)s1);
-            atomicAdd(slot + 2 * nS + P + K + k, (double)s2);
+            red_add_f32(slot + 2 * nS + P + k, s1);
+            red_add_f32(slot + 2 * nS + P + K + k, s2);
         }
     }
 }
@@ -1049,7 +1208,7 @@ __device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, 
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const int k2 = c0 + j;
-                            if (k2 >= r && k2 < K) atomicAdd(slot + 2 * nS + k2 * (k2 + 1) / 2 + r, (double)gv[j]);
+                            if (k2 >= r && k2 < K) red_add_f32(slot + 2 * nS + k2 * (k2 + 1) / 2 + r, gv[j]);
                         }
                     }
                 } else {
@@ -1063,8 +1222,8 @@ __device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, 
                             const int k2 = (c0 >> 1) + j;
                             if (k2 >= k1 && k2 < K) {
                                 const int e = b * P + k2 * (k2 + 1) / 2 + k1;
-                                atomicAdd(slot + 2 * e, (double)(gv[2 * j] + u[2 * j + 1]));
-                                atomicAdd(slot + 2 * e + 1, (double)(gv[2 * j + 1] - u[2 * j]));
+                                red_add_f32(slot + 2 * e, (gv[2 * j] + u[2 * j + 1]));
+                                red_add_f32(slot + 2 * e + 1, (gv[2 * j + 1] - u[2 * j]));
                             }
                         }
                     }
@@ -1085,8 +1244,8 @@ __device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, 
                 s1 = fmaf(wd[j], sQ[k * TILE + j], s1);
                 s2 = fmaf(wt[j], sQW[k * TILE + j], s2);
             }
-            atomicAdd(slot + 2 * nS + P + k, (double)s1);
-            atomicAdd(slot + 2 * nS + P + K + k, (double)s2);
+            red_add_f32(slot + 2 * nS + P + k, s1);
+            red_add_f32(slot + 2 * nS + P + K + k, s2);
         }
     }
 }
@@ -1104,21 +1263,41 @@ __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int 
     float* sPiv = sQW + K * TILE;
     const int lane = threadIdx.x & 31;
     const size_t nfl = tile_floats_rt(K, mr) - 2 * TILE;
-    const int2 tq = g.tiles[tile];
+    const bool grouped = c.group > 1;
+    const int2 tq = grouped ? c.gtiles[tile] : g.tiles[tile];
     if (tq.x < 0 || tq.x >= g.nrings) {
         if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
         __syncthreads();
         return;
     }
     const PivotRing P = pivot_ring(g, tq.x);
-    const int q = tq.y + lane;
-    const long long pix = g.ring_first[P.i] + q;
-    const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
     float2 pv = make_float2(0.0f, 0.0f);
-    if (in) pv = DIRECT ? DirectLoad{c.delta, c.w}(pix) : c.wdw[pix];
-    // lanes past the end of the ring walk the geometry of its last pivot (with zero
-    // weight), which keeps every unwrapped pixel index within [-n_r, 2 n_r)
-    const int qg = min(q, P.n_i - 1);
+    int qg;  // the lane's geometry; lanes past the ring's end: zero weight, valid geometry
+    if (grouped) {
+        // shared neighbour lists: the lane stands for the run of c.group consecutive ring
+        // pixels gi, sits at the run's middle pixel and carries the run's summed weights
+        const int ng = (P.n_i + c.group - 1) / c.group;
+        const int gi = tq.y + lane;
+        const int s0 = min(gi, ng - 1) * c.group, ln = min(c.group, P.n_i - s0);
+        qg = s0 + (ln - 1) / 2;
+        if (gi < ng) {
+            const long long f = g.ring_first[P.i] + s0;
+            for (int u = 0; u < ln; ++u) {
+                const long long pix = f + u;
+                if (pix >= c.piv_lo && pix < c.piv_hi) {
+                    const float2 v = DIRECT ? DirectLoad{c.delta, c.w}(pix) : c.wdw[pix];
+                    pv.x += v.x;
+                    pv.y += v.y;
+                }
+            }
+        }
+    } else {
+        const TilePivot tp = tile_pivot(tq.y, P.n_i, c.quad != 0);
+        const long long pix = g.ring_first[P.i] + tp.q;
+        if (tp.valid && pix >= c.piv_lo && pix < c.piv_hi)
+            pv = DIRECT ? DirectLoad{c.delta, c.w}(pix) : c.wdw[pix];
+        qg = tp.qg;
+    }
     if (!__syncthreads_or(pv.y != 0.0f)) return;
     for (size_t e = threadIdx.x; e < nfl; e += NTHREADS) sA[e] = 0.0f;
     if (threadIdx.x < TILE) {
@@ -1127,10 +1306,12 @@ __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int 
     }
     __syncthreads();
     if (DIRECT)
-        tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW, c.flush, mr);
+        tile_moments<M, SELF>(g, P, qg, DirectLoad{c.delta, c.w}, sA, sW, sQ, sQW, c.flush, mr,
+                              !grouped && c.quad);
     else
-        tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush, mr);
+        tile_moments<M, SELF>(g, P, qg, PackedLoad{c.wdw}, sA, sW, sQ, sQW, c.flush, mr, !grouped && c.quad);
     __syncthreads();
+    if (c.norm != NORM_NONE) tile_normalize<M>(K, sA, sW, c.norm, mr);
     tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF && c.self_subtract, mr);
     __syncthreads();
 }
@@ -1149,12 +1330,12 @@ __device__ __forceinline__ void fwd_tile_tc(const MapDev& g, const MapCall& c, i
         return;
     }
     const PivotRing P = pivot_ring(g, tq.x);
-    const int q = tq.y + lane;
-    const long long pix = g.ring_first[P.i] + q;
-    const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+    const TilePivot tp = tile_pivot(tq.y, P.n_i, c.quad != 0);
+    const long long pix = g.ring_first[P.i] + tp.q;
+    const bool in = tp.valid && pix >= c.piv_lo && pix < c.piv_hi;
     float2 pv = make_float2(0.0f, 0.0f);
     if (in) pv = c.wdw[pix];
-    const int qg = min(q, P.n_i - 1);
+    const int qg = tp.qg;
     if (!__syncthreads_or(pv.y != 0.0f)) return;
     {
         const TcLayout L = tc_layout(K, M, SELF);
@@ -1172,7 +1353,7 @@ __device__ __forceinline__ void fwd_tile_tc(const MapDev& g, const MapCall& c, i
         const int Rm = (2 * K + 7) & ~7, D0 = (M + 1) * Rm;
         const TcLayout L = tc_layout(K, M, SELF);
         tile_moments_l<M, SELF>(g, P, qg, PackedLoad{c.wdw}, LayTC{base, base + L.offQ, base + L.offQW, Rm, D0},
-                                c.flush);
+                                c.flush, M, c.quad != 0);
     }
     __syncthreads();
     tile_contract_tc<M, SELF>(K, base, slot, tc, c.status);
@@ -1286,8 +1467,8 @@ __device__ __forceinline__ void tile_contract_multi(int K, const float* sF, cons
                     si = fmaf(wd[l], fmaf(a, d, -b * cc), si);
                 }
             }
-            atomicAdd(slot + 2 * e, (double)sr);
-            atomicAdd(slot + 2 * e + 1, (double)si);
+            red_add_f32(slot + 2 * e, sr);
+            red_add_f32(slot + 2 * e + 1, si);
         } else {
             const int idx = e - nS, k1 = idx / K, k2 = idx - k1 * K;
             float sd = 0.0f;
@@ -1301,7 +1482,7 @@ __device__ __forceinline__ void tile_contract_multi(int K, const float* sF, cons
                     sd = fmaf(wt[l], W1[l] * W2[l], sd);
                 }
             }
-            atomicAdd(slot + 2 * nS + idx, (double)sd);
+            red_add_f32(slot + 2 * nS + idx, sd);
         }
     }
 }
@@ -1333,9 +1514,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_multi_kernel(MapDev g, Ma
             continue;
         }
         const PivotRing P = pivot_ring(g, tq.x);
-        const int q = tq.y + lane;
-        const long long pix = g.ring_first[P.i] + q;
-        const bool in = (q < P.n_i) && pix >= c.piv_lo && pix < c.piv_hi;
+        const TilePivot tp = tile_pivot(tq.y, P.n_i, true);
+        const long long pix = g.ring_first[P.i] + tp.q;
+        const bool in = tp.valid && pix >= c.piv_lo && pix < c.piv_hi;
         float2 pv[3];
         bool live = false;
 #pragma unroll
@@ -1343,7 +1524,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_multi_kernel(MapDev g, Ma
             pv[f] = in ? arr[f][pix] : make_float2(0.0f, 0.0f);
             live = live || pv[f].y != 0.0f;
         }
-        const int qg = min(q, P.n_i - 1);
+        const int qg = tp.qg;
         if (!__syncthreads_or(live)) continue;
         for (size_t e = threadIdx.x; e < 3 * fsz; e += NTHREADS) sF[e] = 0.0f;
         if (threadIdx.x < TILE) {
@@ -1357,7 +1538,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) map_fwd_multi_kernel(MapDev g, Ma
         for (int f = 0; f < 3; ++f) {
             float* sA = sF + f * fsz;
             tile_moments<M, false>(g, P, qg, PackedLoad{arr[f]}, sA, sA + (size_t)K * (M + 1) * 2 * TILE, nullptr,
-                                   nullptr, c.flush);
+                                   nullptr, c.flush, M, true);
         }
         __syncthreads();
         tile_contract_multi<M>(K, sF, sPiv, slot);

@@ -135,6 +135,8 @@ extern "C" tpcf_status tpcf_forward_noalloc(tpcf_plan plan, const float* d_delta
     c.counter = counter;
     c.status = plan->status;
     c.self_subtract = 0;
+    c.norm = norm_of_flags(plan->flags);
+    c.quad = plan->tune_fwd.quad;
     c.flush = plan->tune_fwd.flush;
     c.tile_lo = 0;  // every tile; those without a pivot in range return at once
     c.tile_hi = plan->map.ntiles;

@@ -43,8 +43,9 @@ struct tpcf_plan_s {
     // launch configuration of the map pair kernels (defaults, or picked by the autotuner):
     // register variant (CTAs per SM the registers are sized for), CTAs per SM launched,
     // rings summed in registers per shared-memory flush
+    // and, for the forward, the tile layout (1: quarter-turn runs, 0: consecutive pivots)
     struct Tune {
-        int variant = 3, ctas = 0, flush = 8;
+        int variant = 3, ctas = 0, flush = 8, quad = 1;
     } tune_fwd, tune_bwd;
     bool tuned = false;
     // per-call scratch
@@ -62,6 +63,10 @@ struct tpcf_plan_s {
     double* mslots = nullptr;
     double* msums = nullptr;
     int multi_grid = 0;
+    // shared-neighbour-list forward: tile list of the last group size used
+    int2* gtiles = nullptr;
+    int64_t ngtiles = 0, gtiles_cap = 0;
+    int ggroup = 0;
     // staging for tpcf_run_host
     float* st_delta = nullptr;
     float* st_w = nullptr;

@@ -81,10 +81,24 @@ struct MapCall {
     int self_subtract;      // subtract the j = k self term
     int flush;              // rings summed in registers before a shared-memory flush (tuned)
     int64_t tile_lo, tile_hi;  // tiles that can hold a pivot of [piv_lo, piv_hi)
+    int norm;               // NORM_*: per-pivot normalisation of the moments before the contraction
+    int quad;               // forward tiles in the quarter-turn layout (tile_pivot)
+    int group;              // > 1: shared neighbour lists, one lane per run of `group` ring pixels
+    const int2* gtiles;     // group > 1: tiles (ring, first run of the tile)
 };
 
 // One plan of a batch (device-resident): its geometry, its per-call arguments and
 // the index of its first tile in the batch's concatenated work queue.
+// Per-pivot normalisation of the moments (MapCall::norm): none (zeta = S / D), each
+// bin by its own weight W^k(i), or every bin by the pivot's total sum_k W^k(i).
+constexpr int NORM_NONE = 0;
+constexpr int NORM_BIN_MEAN = 1;
+constexpr int NORM_PIVOT_TOTAL = 2;
+constexpr uint32_t NORM_FLAGS = TPCF_NORM_BIN_MEAN | TPCF_NORM_PIVOT_TOTAL;
+inline int norm_of_flags(uint32_t flags) {
+    return (flags & TPCF_NORM_BIN_MEAN) ? NORM_BIN_MEAN : ((flags & TPCF_NORM_PIVOT_TOTAL) ? NORM_PIVOT_TOTAL : NORM_NONE);
+}
+
 constexpr int TPCF_MAX_BATCH = 256;
 struct BatchItem {
     MapDev g;

@@ -43,7 +43,7 @@ static std::string tune_key(const tpcf_plan_s* P) {
     std::string name(prop.name);
     for (char& c : name)
         if (c == ' ') c = '_';
-    snprintf(buf, sizeof(buf), "v1 dev=%s sms=%d map nside=%d K=%d M=%d flags=%u edges=%016llx", name.c_str(),
+    snprintf(buf, sizeof(buf), "v2 dev=%s sms=%d map nside=%d K=%d M=%d flags=%u edges=%016llx", name.c_str(),
              P->num_sms, P->map.nside, P->K, P->M, P->flags, h);
     return buf;
 }
@@ -60,8 +60,8 @@ static bool cache_lookup(const std::string& key, tpcf_plan_s::Tune* f, tpcf_plan
         const size_t n = key.size();
         if (strncmp(line, key.c_str(), n) != 0 || line[n] != '|') continue;
         tpcf_plan_s::Tune tf, tb;
-        if (sscanf(line + n + 1, " fwd %d %d %d bwd %d %d %d", &tf.variant, &tf.ctas, &tf.flush, &tb.variant,
-                   &tb.ctas, &tb.flush) == 6) {
+        if (sscanf(line + n + 1, " fwd %d %d %d %d bwd %d %d %d", &tf.variant, &tf.ctas, &tf.flush, &tf.quad,
+                   &tb.variant, &tb.ctas, &tb.flush) == 7) {
             *f = tf;
             *b = tb;
             found = true;  // the last matching line wins
@@ -76,14 +76,14 @@ static void cache_store(const std::string& key, const tpcf_plan_s::Tune& f, cons
     if (!path || !*path) return;
     FILE* fp = fopen(path, "a");
     if (!fp) return;
-    fprintf(fp, "%s| fwd %d %d %d bwd %d %d %d\n", key.c_str(), f.variant, f.ctas, f.flush, b.variant, b.ctas,
-            b.flush);
+    fprintf(fp, "%s| fwd %d %d %d %d bwd %d %d %d\n", key.c_str(), f.variant, f.ctas, f.flush, f.quad, b.variant,
+            b.ctas, b.flush);
     fclose(fp);
 }
 
 static bool valid(const tpcf_plan_s* P, const tpcf_plan_s::Tune& t, bool bwd) {
     if (t.variant != 2 && t.variant != 3) return false;
-    if (t.flush < 1 || t.flush > 64 || t.ctas < 1) return false;
+    if (t.flush < 1 || t.flush > 64 || t.ctas < 1 || t.quad < 0 || t.quad > 1) return false;
     const int self = (P->flags & TPCF_SELF_PAIRS_SUBTRACT) ? 1 : 0;
     const int occ = bwd ? map_bwd_occupancy(P->M, P->K, t.variant) : map_fwd_occupancy(P->M, P->K, self, t.variant);
     return t.ctas <= occ;
@@ -115,6 +115,7 @@ extern "C" tpcf_status tpcf_plan_autotune(tpcf_plan plan, const float* d_delta, 
         set_error("tpcf_plan_autotune: map plans with the FP32 contraction only");
         return TPCF_ERR_UNSUPPORTED;
     }
+    if (P->flags & NORM_FLAGS) passes &= 1;  // no adjoint for these plans
     const std::string key = tune_key(P);
     {
         tpcf_plan_s::Tune f, b;
@@ -179,6 +180,30 @@ extern "C" tpcf_status tpcf_plan_autotune(tpcf_plan plan, const float* d_delta, 
         const tpcf_plan_s::Tune keep = T;
         tpcf_plan_s::Tune best = keep;
         float best_ms = 1e30f;
+        // times the configuration in T (the first of three runs warms up) and keeps the best
+        auto try_config = [&]() {
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3 && st == TPCF_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                for (auto& sl : sample) {
+                    st = bwd ? tpcf_backward(P, d_delta, d_w, sl.first, sl.second, norm, dL, grad, s)
+                             : tpcf_forward(P, d_delta, d_w, sl.first, sl.second, zeta, norm, nullptr, s);
+                    if (st != TPCF_OK) break;
+                }
+                cudaEventRecord(e1, s);
+                if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) {
+                    fail(ce, "tpcf_plan_autotune timing");
+                    break;
+                }
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, t);
+            }
+            if (st == TPCF_OK && ms < best_ms) {
+                best_ms = ms;
+                best = T;
+            }
+        };
         for (int variant = 3; variant >= 2 && st == TPCF_OK; --variant) {
             const int occ = bwd ? map_bwd_occupancy(M, K, variant) : map_fwd_occupancy(M, K, self, variant);
             for (int ctas = occ; ctas >= std::max(1, occ - 1) && st == TPCF_OK; --ctas) {
@@ -187,29 +212,14 @@ extern "C" tpcf_status tpcf_plan_autotune(tpcf_plan plan, const float* d_delta, 
                     T.variant = variant;
                     T.ctas = ctas;
                     T.flush = flushes[fi];
-                    float ms = 1e30f;
-                    for (int rep = 0; rep < 3 && st == TPCF_OK; ++rep) {
-                        cudaEventRecord(e0, s);
-                        for (auto& sl : sample) {
-                            st = bwd ? tpcf_backward(P, d_delta, d_w, sl.first, sl.second, norm, dL, grad, s)
-                                     : tpcf_forward(P, d_delta, d_w, sl.first, sl.second, zeta, norm, nullptr, s);
-                            if (st != TPCF_OK) break;
-                        }
-                        cudaEventRecord(e1, s);
-                        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) {
-                            fail(ce, "tpcf_plan_autotune timing");
-                            break;
-                        }
-                        float t = 0.0f;
-                        cudaEventElapsedTime(&t, e0, e1);
-                        if (rep > 0) ms = std::min(ms, t);  // the first run warms up
-                    }
-                    if (st == TPCF_OK && ms < best_ms) {
-                        best_ms = ms;
-                        best = T;
-                    }
+                    try_config();
                 }
             }
+        }
+        if (!bwd && st == TPCF_OK) {  // the forward's tile layout, at the best shape
+            T = best;
+            T.quad = 1 - best.quad;
+            try_config();
         }
         T = st == TPCF_OK ? best : keep;
     }
@@ -228,23 +238,24 @@ extern "C" tpcf_status tpcf_plan_autotune(tpcf_plan plan, const float* d_delta, 
     return tpcf_plan_sync(P);
 }
 
-extern "C" tpcf_status tpcf_plan_launch_config(tpcf_plan plan, int32_t* out6) {
-    if (!plan || !out6) return TPCF_ERR_INVALID_ARG;
+extern "C" tpcf_status tpcf_plan_launch_config(tpcf_plan plan, int32_t* out7) {
+    if (!plan || !out7) return TPCF_ERR_INVALID_ARG;
     const tpcf_plan_s* P = plan;
-    out6[0] = P->tune_fwd.variant;
-    out6[1] = P->tune_fwd.ctas;
-    out6[2] = P->tune_fwd.flush;
-    out6[3] = P->tune_bwd.variant;
-    out6[4] = P->tune_bwd.ctas;
-    out6[5] = P->tune_bwd.flush;
+    out7[0] = P->tune_fwd.variant;
+    out7[1] = P->tune_fwd.ctas;
+    out7[2] = P->tune_fwd.flush;
+    out7[3] = P->tune_fwd.quad;
+    out7[4] = P->tune_bwd.variant;
+    out7[5] = P->tune_bwd.ctas;
+    out7[6] = P->tune_bwd.flush;
     return TPCF_OK;
 }
 
-extern "C" tpcf_status tpcf_plan_set_launch_config(tpcf_plan plan, const int32_t* in6) {
-    if (!plan || !in6) return TPCF_ERR_INVALID_ARG;
+extern "C" tpcf_status tpcf_plan_set_launch_config(tpcf_plan plan, const int32_t* in7) {
+    if (!plan || !in7) return TPCF_ERR_INVALID_ARG;
     tpcf_plan_s* P = plan;
     if (P->kind != PLAN_MAP || (P->flags & TPCF_CONTRACT_TC)) return TPCF_ERR_UNSUPPORTED;
-    tpcf_plan_s::Tune f{in6[0], in6[1], in6[2]}, b{in6[3], in6[4], in6[5]};
+    tpcf_plan_s::Tune f{in7[0], in7[1], in7[2], in7[3]}, b{in7[4], in7[5], in7[6], 0};
     if (!valid(P, f, false) || !valid(P, b, true)) return TPCF_ERR_INVALID_ARG;
     P->tune_fwd = f;
     P->tune_bwd = b;

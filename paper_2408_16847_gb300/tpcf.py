@@ -46,7 +46,8 @@ class Plan:
 
     # -- construction
     @staticmethod
-    def _bins(edges_deg=None, edges_rad=None, m_max: int = 0, self_pairs: str = "keep", contract: str = "fp32"):
+    def _bins(edges_deg=None, edges_rad=None, m_max: int = 0, self_pairs: str = "keep", contract: str = "fp32",
+              norm: str = "default"):
         if edges_rad is None:
             edges_rad = np.deg2rad(np.asarray(edges_deg, dtype=np.float64))
         e = np.ascontiguousarray(edges_rad, dtype=np.float64)
@@ -57,13 +58,19 @@ class Plan:
             raise ValueError(self_pairs)
         if contract == "tc":
             flags |= _capi.CONTRACT_TC
+        if norm == "bin_mean":
+            flags |= _capi.NORM_BIN_MEAN
+        elif norm == "pivot_total":
+            flags |= _capi.NORM_PIVOT_TOTAL
+        elif norm != "default":
+            raise ValueError(norm)
         b = _capi.Bins(len(e) - 1, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(m_max), flags)
         return b, e, flags
 
     @classmethod
     def map(cls, nside: int, edges_deg=None, m_max: int = 0, *, edges_rad=None, self_pairs: str = "keep",
-            contract: str = "fp32", stream=None) -> "Plan":
-        b, e, flags = cls._bins(edges_deg, edges_rad, m_max, self_pairs, contract)
+            contract: str = "fp32", norm: str = "default", stream=None) -> "Plan":
+        b, e, flags = cls._bins(edges_deg, edges_rad, m_max, self_pairs, contract, norm)
         h = ctypes.c_void_p()
         check(lib().tpcf_plan_create_map(ctypes.byref(h), int(nside), ctypes.byref(b), _stream_ptr(stream)),
               "tpcf_plan_create_map")
@@ -71,10 +78,10 @@ class Plan:
 
     @classmethod
     def catalog(cls, xyz: torch.Tensor, edges_deg=None, m_max: int = 0, *, edges_rad=None,
-                self_pairs: str = "keep", contract: str = "fp32", stream=None) -> "Plan":
+                self_pairs: str = "keep", contract: str = "fp32", norm: str = "default", stream=None) -> "Plan":
         n = xyz.shape[0]
         _need(xyz, torch.float64, 3 * n, "xyz")
-        b, e, flags = cls._bins(edges_deg, edges_rad, m_max, self_pairs, contract)
+        b, e, flags = cls._bins(edges_deg, edges_rad, m_max, self_pairs, contract, norm)
         h = ctypes.c_void_p()
         check(lib().tpcf_plan_create_catalog(ctypes.byref(h), _ptr(xyz), n, ctypes.byref(b),
                                              _stream_ptr(stream)), "tpcf_plan_create_catalog")
@@ -112,6 +119,24 @@ class Plan:
         sums = torch.empty(self.zeta_shape(), dtype=torch.float64, device=dev) if want_sums else None
         check(lib().tpcf_forward(self._h, _ptr(delta), _ptr(w), lo, hi, _ptr(zeta), _ptr(norm), _ptr(sums),
                                  _stream_ptr(stream)), "tpcf_forward")
+        if want_sums:
+            return zeta, norm, sums
+        return zeta, norm
+
+    def forward_grouped(self, delta: torch.Tensor, w: torch.Tensor, group: int,
+                        pivots: Optional[Tuple[int, int]] = None, want_sums: bool = False, stream=None):
+        """Shared-neighbour-list forward (tpcf_forward_grouped): runs of `group` ring pixels
+        take the moments of their middle pixel.  Returns as forward()."""
+        n = self.npoints
+        _need(delta, torch.float32, n, "delta")
+        _need(w, torch.float32, n, "w")
+        lo, hi = (0, n) if pivots is None else (int(pivots[0]), int(pivots[1]))
+        dev = delta.device
+        zeta = torch.empty(self.zeta_shape(), dtype=torch.float64, device=dev)
+        norm = torch.empty((self.K, self.K), dtype=torch.float64, device=dev)
+        sums = torch.empty(self.zeta_shape(), dtype=torch.float64, device=dev) if want_sums else None
+        check(lib().tpcf_forward_grouped(self._h, _ptr(delta), _ptr(w), int(group), lo, hi, _ptr(zeta), _ptr(norm),
+                                         _ptr(sums), _stream_ptr(stream)), "tpcf_forward_grouped")
         if want_sums:
             return zeta, norm, sums
         return zeta, norm
@@ -174,15 +199,16 @@ class Plan:
         return self.launch_config()
 
     def launch_config(self) -> dict:
-        c = (ctypes.c_int32 * 6)()
+        """forward: variant, ctas_per_sm, flush_rings, quarter_turn_tiles; adjoint: the first three."""
+        c = (ctypes.c_int32 * 7)()
         check(lib().tpcf_plan_launch_config(self._h, c), "tpcf_plan_launch_config")
-        return {"forward": {"variant": c[0], "ctas_per_sm": c[1], "flush_rings": c[2]},
-                "adjoint": {"variant": c[3], "ctas_per_sm": c[4], "flush_rings": c[5]}}
+        return {"forward": {"variant": c[0], "ctas_per_sm": c[1], "flush_rings": c[2], "quarter_turn_tiles": c[3]},
+                "adjoint": {"variant": c[4], "ctas_per_sm": c[5], "flush_rings": c[6]}}
 
     def set_launch_config(self, cfg: dict) -> None:
         f, b = cfg["forward"], cfg["adjoint"]
-        c = (ctypes.c_int32 * 6)(f["variant"], f["ctas_per_sm"], f["flush_rings"], b["variant"], b["ctas_per_sm"],
-                                 b["flush_rings"])
+        c = (ctypes.c_int32 * 7)(f["variant"], f["ctas_per_sm"], f["flush_rings"], f.get("quarter_turn_tiles", 1),
+                                 b["variant"], b["ctas_per_sm"], b["flush_rings"])
         check(lib().tpcf_plan_set_launch_config(self._h, c), "tpcf_plan_set_launch_config")
 
     def halo(self, begin: int, end: int) -> Tuple[int, int]:
@@ -251,6 +277,20 @@ def normalize(sums: torch.Tensor, norm: torch.Tensor, scale: float = 1.0, stream
     zeta = torch.empty_like(sums)
     check(lib().tpcf_normalize(_ptr(sums), _ptr(norm), float(scale), K, M1 - 1, _ptr(zeta), _stream_ptr(stream)),
           "tpcf_normalize")
+    return zeta
+
+
+def edge_correct(sums: torch.Tensor, rsums: torch.Tensor, scale: float = 1.0, stream=None) -> torch.Tensor:
+    """m-coupling correction (tpcf_edge_correct): sums (M+1,K,K,2) of the D - R run,
+    rsums (>= 2M+1,K,K,2) of the randoms' delta = 1 run; returns zeta (M+1,K,K,2)."""
+    M1, K = sums.shape[0], sums.shape[1]
+    _need(sums, torch.float64, M1 * K * K * 2, "sums")
+    if rsums.shape[0] < 2 * M1 - 1 or rsums.shape[1:] != sums.shape[1:]:
+        raise ValueError("rsums needs multipoles 0..2M with the same bins")
+    _need(rsums, torch.float64, rsums.shape[0] * K * K * 2, "rsums")
+    zeta = torch.empty_like(sums)
+    check(lib().tpcf_edge_correct(_ptr(sums), _ptr(rsums), float(scale), K, M1 - 1, _ptr(zeta), _stream_ptr(stream)),
+          "tpcf_edge_correct")
     return zeta
 
 

@@ -27,6 +27,14 @@ def test_header_declares_what_binding_lists():
     assert _declared() == sorted(_capi.EXPORTS)
 
 
+def test_flag_constants_match_the_header():
+    from paper_2408_16847_gb300 import _capi
+    src = open(os.path.join(ROOT, "include", "tpcf.h")).read()
+    flags = dict((k, int(v)) for k, v in re.findall(r"#define TPCF_([A-Z0-9_]+) (\d+)u", src))
+    for name in ("SELF_PAIRS_SUBTRACT", "CONTRACT_TC", "NORM_BIN_MEAN", "NORM_PIVOT_TOTAL"):
+        assert getattr(_capi, name) == flags[name], name
+
+
 def test_every_declared_symbol_is_exported(lib):
     for name in _declared():
         assert hasattr(lib, name), name
@@ -64,4 +72,17 @@ def test_invalid_arguments_need_no_gpu(lib):
     assert lib.tpcf_batch_launch(None, None) == 1
     assert lib.tpcf_batch_kernel_launches(None) == -1
     lib.tpcf_batch_destroy(None)
+    # both per-pivot normalisations at once; a normalisation with self-pair subtraction
+    b5 = _capi.Bins(2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4,
+                    _capi.NORM_BIN_MEAN | _capi.NORM_PIVOT_TOTAL)
+    assert lib.tpcf_plan_create_map(ctypes.byref(h), 8, ctypes.byref(b5), None) == 1
+    b6 = _capi.Bins(2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4,
+                    _capi.NORM_BIN_MEAN | _capi.SELF_PAIRS_SUBTRACT)
+    assert lib.tpcf_plan_create_map(ctypes.byref(h), 8, ctypes.byref(b6), None) == 5
+    one = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    assert lib.tpcf_edge_correct(None, one, 1.0, 2, 2, one, None) == 1
+    assert lib.tpcf_edge_correct(one, one, 1.0, 2, 17, one, None) == 1
+    assert lib.tpcf_edge_correct(one, one, 0.0, 2, 2, one, None) == 1
+    assert lib.tpcf_edge_correct(one, one, 1.0, 33, 2, one, None) == 1
+    assert lib.tpcf_forward_grouped(None, one, one, 3, 0, 1, one, one, None, None) == 1
     assert h.value is None

@@ -46,7 +46,8 @@ def test_every_configuration_matches_the_oracle(cuda_device):
     for variant in (3, 2):
         for ctas in (1, 2, 3):
             for flush in (4, 8, 16):
-                cfg = {"forward": {"variant": variant, "ctas_per_sm": ctas, "flush_rings": flush},
+                cfg = {"forward": {"variant": variant, "ctas_per_sm": ctas, "flush_rings": flush,
+                                   "quarter_turn_tiles": 0 if flush == 8 else 1},
                        "adjoint": {"variant": variant, "ctas_per_sm": ctas, "flush_rings": flush}}
                 try:
                     plan.set_launch_config(cfg)
@@ -62,6 +63,14 @@ def test_every_configuration_matches_the_oracle(cuda_device):
                 assert np.abs(grad - gref).max() < TOL * np.abs(gref).max(), cfg
                 seen += 1
     assert seen >= 6
+    # both tile layouts on a pivot range that starts and ends inside rings
+    pref = oracle.zeta(xyz, d.astype(np.float64), w.astype(np.float64), EDGES, M, pivots=np.arange(1000, 3333))
+    for layout in (0, 1):
+        cfg = plan.launch_config()
+        cfg["forward"]["quarter_turn_tiles"] = layout
+        plan.set_launch_config(cfg)
+        zeta, _ = plan.forward(dt, wt, (1000, 3333))
+        assert rel_err_per_m(tpcf.as_complex(zeta).cpu().numpy(), pref["zeta"]).max() < TOL, layout
     plan.set_launch_config(base)
     plan.close()
 
@@ -77,6 +86,7 @@ def test_autotune_picks_a_valid_configuration_and_caches_it(cuda_device, tmp_pat
     for p in ("forward", "adjoint"):
         assert cfg[p]["variant"] in (2, 3) and 1 <= cfg[p]["ctas_per_sm"] <= 3
         assert cfg[p]["flush_rings"] in (4, 8, 16)
+    assert cfg["forward"]["quarter_turn_tiles"] in (0, 1)
     text = cache.read_text()
     assert "nside=32" in text and "K=6" in text and "M=8" in text
     # a new plan with the same key starts from the cached configuration
