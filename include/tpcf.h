@@ -194,7 +194,7 @@ tpcf_status tpcf_forward_grouped(tpcf_plan plan, const float* d_delta, const flo
 
 /*
  * Multi-field forward (end of Sec. 2, after eq. ubEstimator): three fields A, B, C on
- * the pixels of one map plan (e.g. tomographic bins), each with its own weights.  With
+ * the points of one plan (e.g. tomographic bins), each with its own weights.  With
  * the moments a^k(i; F), W^k(i; F) of eq. Xm.binned taken over field F, and summed over
  * the cyclic permutations (P, X, Y) of (A, B, C):
  *   S_m(k1,k2) = sum_(P,X,Y) sum_i w^P_i P_i a_m^{k1}(i; X) conj(a_m^{k2}(i; Y)),
@@ -203,9 +203,11 @@ tpcf_status tpcf_forward_grouped(tpcf_plan plan, const float* d_delta, const flo
  * over the pivots in [pivot_begin, pivot_end).  With A = B = C this is the single-field
  * estimate.  The sums are full K x K matrices (not Hermitian when the fields differ):
  * d_zeta and d_sums (optional) (m_max+1) x K x K x {re, im} doubles, d_norm K x K.
- * Map plans with the FP32 contraction and self pairs kept (else TPCF_ERR_UNSUPPORTED,
- * also when the three fields' tile moments do not fit in shared memory).  The first
- * call allocates the plan's buffers for fields B and C (2 x 8 bytes per pixel).
+ * Map and catalogue plans (the fields indexed like the plan's pixels or points) with
+ * the FP32 contraction, self pairs kept and the default normalisation (else
+ * TPCF_ERR_UNSUPPORTED, also when the three fields' tile moments do not fit in shared
+ * memory).  The first call allocates the plan's buffers for fields B and C (2 x 8
+ * bytes per point).
  */
 tpcf_status tpcf_forward_multi(tpcf_plan plan, const float* d_delta_a, const float* d_w_a,
                                const float* d_delta_b, const float* d_w_b, const float* d_delta_c,

@@ -63,6 +63,8 @@ tpcf_status catalog_backward(tpcf_plan_s* P, const float* d_delta, const float* 
                              const double* d_norm, const double* d_dL, float* d_grad, cudaStream_t s);
 tpcf_status catalog_forward(tpcf_plan_s* P, const float* d_delta, const float* d_w, int64_t lo, int64_t hi,
                             double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s);
+tpcf_status catalog_forward_multi(tpcf_plan_s* P, const float* const* d_delta, const float* const* d_w, int64_t lo,
+                                  int64_t hi, double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s);
 // loads the allocation-free forward's scratch array on a device (noalloc.cu)
 tpcf_status noalloc_prepare(int dev);
 
@@ -511,12 +513,18 @@ extern "C" tpcf_status tpcf_forward_multi(tpcf_plan plan, const float* d_delta_a
         return TPCF_ERR_INVALID_ARG;
     if (pivot_begin < 0 || pivot_end < pivot_begin || pivot_end > plan->npoints) return TPCF_ERR_INVALID_ARG;
     tpcf_plan_s* P = plan;
-    if (P->kind != PLAN_MAP || (P->flags & (TPCF_CONTRACT_TC | TPCF_SELF_PAIRS_SUBTRACT | NORM_FLAGS))) {
-        set_error("tpcf_forward_multi: map plans with the FP32 contraction, self pairs kept");
+    if (P->flags & (TPCF_CONTRACT_TC | TPCF_SELF_PAIRS_SUBTRACT | NORM_FLAGS)) {
+        set_error("tpcf_forward_multi: plans with the FP32 contraction, self pairs kept, default normalisation");
         return TPCF_ERR_UNSUPPORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
     P->last_stream = s;
+    if (P->kind == PLAN_CATALOG) {
+        const float* dd[3] = {d_delta_a, d_delta_b, d_delta_c};
+        const float* ww[3] = {d_w_a, d_w_b, d_w_c};
+        return catalog_forward_multi(P, dd, ww, pivot_begin, pivot_end, d_zeta, d_norm, d_sums, s);
+    }
+    if (P->kind != PLAN_MAP) return TPCF_ERR_UNSUPPORTED;
     const MapDev& g = P->map;
     const int K = P->K, M = P->M;
     const int nent = n_entries_multi(K, M);

@@ -391,6 +391,56 @@ __device__ __forceinline__ void cat_walk_grouped(const CatDev& g, const float2* 
     }
 }
 
+// The tile's moments over the catalogue walk (the body of the forward): every warp
+// walks its share of the cap's candidates for the lane's pivot P with the neighbour
+// values `wdw` and adds its register sums into the tile's shared moments once per bin
+// and chunk.  The caller zeroes the moments before and synchronises after.
+template <int M, bool SELF>
+__device__ __forceinline__ void cat_tile_moments(const CatDev& g, const float2* __restrict__ wdw,
+                                                 const float* s_cap, const CatPivot& P, const float* sE2,
+                                                 const unsigned char* slut, float4* sCh, float4* sCl, float2* sCv,
+                                                 float* sA, float* sW, float* sQ, float* sQW) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 acc[M + 1];
+#pragma unroll
+    for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
+    float W = 0.0f, Qs = 0.0f, QW = 0.0f;
+    cat_walk_grouped(
+        g, wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
+        [&](bool active, int, float dx, float dy, float dz, float2 v, int) {
+            const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+            const float E = fmaf(dx, P.ex, dy * P.ey);
+            const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+            const float wd = active ? v.x : 0.0f;
+            const float ww = active ? v.y : 0.0f;
+            harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
+            W += ww;
+            if (SELF) {
+                Qs = fmaf(wd, wd, Qs);
+                QW = fmaf(ww, ww, QW);
+            }
+        },
+        [&](int k, bool had) {
+            if (had) {
+                cat_flush<M, SELF>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
+            }
+        },
+        [&](int k, float dx, float dy, float dz, float2 v, int) {
+            // every group is flushed by now, so the register sums are free
+            const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
+            const float E = fmaf(dx, P.ex, dy * P.ey);
+            const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
+            harmonics<M>(acc, N * rinv, E * rinv, v.x, v.x);
+            W = v.y;
+            if (SELF) {
+                Qs = v.x * v.x;
+                QW = v.y * v.y;
+            }
+            cat_flush<M, SELF>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
+        },
+        [&](int64_t, int) {});
+}
+
 template <int M, bool SELF>
 __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall c) {
     extern __shared__ __align__(16) float smem[];
@@ -439,47 +489,83 @@ __global__ void __launch_bounds__(NTHREADS, 3) cat_fwd_kernel(CatDev g, MapCall 
         if (warp == 0) cat_tile_cap(g, live, P, s_cap);
         __syncthreads();
 
-        float2 acc[M + 1];
-#pragma unroll
-        for (int m = 0; m <= M; ++m) acc[m] = make_float2(0.0f, 0.0f);
-        float W = 0.0f, Qs = 0.0f, QW = 0.0f;
-        cat_walk_grouped(
-            g, c.wdw, s_cap, P, sE2, slut, sCh + warp * TILE, sCl + warp * TILE, sCv + warp * TILE,
-            [&](bool active, int, float dx, float dy, float dz, float2 v, int) {
-                const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
-                const float E = fmaf(dx, P.ex, dy * P.ey);
-                const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
-                const float wd = active ? v.x : 0.0f;
-                const float ww = active ? v.y : 0.0f;
-                harmonics<M>(acc, N * rinv, E * rinv, wd, wd);
-                W += ww;
-                if (SELF) {
-                    Qs = fmaf(wd, wd, Qs);
-                    QW = fmaf(ww, ww, QW);
-                }
-            },
-            [&](int k, bool had) {
-                if (had) {
-                    cat_flush<M, SELF>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
-                }
-            },
-            [&](int k, float dx, float dy, float dz, float2 v, int) {
-                // every group is flushed by now, so the register sums are free
-                const float N = fmaf(dx, P.nx, fmaf(dy, P.ny, dz * P.nz));
-                const float E = fmaf(dx, P.ex, dy * P.ey);
-                const float rinv = rsqrtf(fmaxf(fmaf(N, N, E * E), 1e-30f));
-                harmonics<M>(acc, N * rinv, E * rinv, v.x, v.x);
-                W = v.y;
-                if (SELF) {
-                    Qs = v.x * v.x;
-                    QW = v.y * v.y;
-                }
-                cat_flush<M, SELF>(sA, sW, sQ, sQW, k, lane, acc, W, Qs, QW);
-            },
-            [&](int64_t, int) {});
+        cat_tile_moments<M, SELF>(g, c.wdw, s_cap, P, sE2, slut, sCh, sCl, sCv, sA, sW, sQ, sQW);
         __syncthreads();
         if (c.norm != NORM_NONE) tile_normalize<M>(K, sA, sW, c.norm);
         tile_contract<M>(K, sA, sW, sQ, sQW, sPiv, slot, SELF);
+        __syncthreads();
+    }
+}
+
+// Multi-field forward on a catalogue (tpcf_forward_multi): three fields on the same
+// points, each with its own weights.  The tile's cap is walked once per field (the
+// moments of the neighbour fields A, B, C), and tile_contract_multi forms the cyclic
+// sum over the pivot field.  Shared memory: the three fields' moments, the pivots'
+// three (w d, w), and the per-warp candidate staging.
+template <int M>
+__host__ __device__ inline size_t cat_multi_bytes(int K) {
+    return multi_tile_floats(K, M) * sizeof(float) + (size_t)NWARPS * TILE * (2 * sizeof(float4) + sizeof(float2));
+}
+
+template <int M>
+__global__ void __launch_bounds__(NTHREADS, 1) cat_fwd_multi_kernel(CatDev g, MapCall c,
+                                                                    const float2* __restrict__ wdwB,
+                                                                    const float2* __restrict__ wdwC) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_tile;
+    __shared__ float s_cap[5];
+    __shared__ float sE2[TPCF_MAX_BINS + 1];
+    __shared__ unsigned char slut[CAT_LUT];
+    const int K = g.K;
+    const size_t fsz = multi_field_floats(K, M);
+    float* sF = smem;
+    float* sPiv = smem + 3 * fsz;  // [field][w d, w][32]
+    float4* sCh = reinterpret_cast<float4*>(smem + multi_tile_floats(K, M));
+    float4* sCl = sCh + NWARPS * TILE;
+    float2* sCv = reinterpret_cast<float2*>(sCl + NWARPS * TILE);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e <= K; e += NTHREADS) sE2[e] = g.E2[e];
+    for (int e = threadIdx.x; e < CAT_LUT; e += NTHREADS) slut[e] = g.lut[e];
+    double* slot = c.slots + (size_t)blockIdx.x * n_entries_multi(K, M);
+    const float2* arr[3] = {c.wdw, wdwB, wdwC};
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(c.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if ((long long)tile >= g.ntiles) break;
+        const int64_t si = (int64_t)tile * TILE + lane;
+        float2 pv[3] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+        bool live = false;
+        if (si < g.n) {
+            const int64_t o = g.orig[si];
+            if (o >= c.piv_lo && o < c.piv_hi) {
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    pv[f] = arr[f][si];
+                    live = live || pv[f].y != 0.0f;
+                }
+            }
+        }
+        if (!__syncthreads_or(live)) continue;
+        for (size_t e = threadIdx.x; e < 3 * fsz; e += NTHREADS) sF[e] = 0.0f;
+        if (threadIdx.x < TILE) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                sPiv[f * 2 * TILE + lane] = pv[f].x;
+                sPiv[f * 2 * TILE + TILE + lane] = pv[f].y;
+            }
+        }
+        const CatPivot P = cat_pivot(g, si < g.n ? si : -1);
+        if (warp == 0) cat_tile_cap(g, live, P, s_cap);
+        __syncthreads();
+#pragma unroll 1
+        for (int f = 0; f < 3; ++f) {
+            float* sA = sF + f * fsz;
+            cat_tile_moments<M, false>(g, arr[f], s_cap, P, sE2, slut, sCh, sCl, sCv, sA,
+                                       sA + (size_t)K * (M + 1) * 2 * TILE, nullptr, nullptr);
+        }
+        __syncthreads();
+        tile_contract_multi<M>(K, sF, sPiv, slot);
         __syncthreads();
     }
 }

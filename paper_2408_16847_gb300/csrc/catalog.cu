@@ -24,7 +24,10 @@ namespace tpcf {
     cudaError_t cat_fwd_launch_m##m(const CatDev&, const MapCall&, int, cudaStream_t);        \
     int cat_fwd_occupancy_m##m(int, int);                                                     \
     cudaError_t cat_bwd_launch_m##m(const CatDev&, const MapCall&, int, cudaStream_t);        \
-    int cat_bwd_occupancy_m##m(int);
+    int cat_bwd_occupancy_m##m(int);                                                          \
+    cudaError_t cat_fwd_multi_launch_m##m(const CatDev&, const MapCall&, const float2*, const float2*, int, \
+                                          cudaStream_t);                                      \
+    int cat_fwd_multi_occupancy_m##m(int);
 TPCF_DECL_CAT_M(0) TPCF_DECL_CAT_M(1) TPCF_DECL_CAT_M(2) TPCF_DECL_CAT_M(3) TPCF_DECL_CAT_M(4)
 TPCF_DECL_CAT_M(5) TPCF_DECL_CAT_M(6) TPCF_DECL_CAT_M(7) TPCF_DECL_CAT_M(8) TPCF_DECL_CAT_M(9)
 TPCF_DECL_CAT_M(10) TPCF_DECL_CAT_M(11) TPCF_DECL_CAT_M(12) TPCF_DECL_CAT_M(13) TPCF_DECL_CAT_M(14)
@@ -36,8 +39,12 @@ struct CLaunch {
     int (*occ)(int, int);
     cudaError_t (*bwd)(const CatDev&, const MapCall&, int, cudaStream_t);
     int (*bwd_occ)(int);
+    cudaError_t (*multi)(const CatDev&, const MapCall&, const float2*, const float2*, int, cudaStream_t);
+    int (*multi_occ)(int);
 };
-#define TPCF_CROW(m) {cat_fwd_launch_m##m, cat_fwd_occupancy_m##m, cat_bwd_launch_m##m, cat_bwd_occupancy_m##m}
+#define TPCF_CROW(m)                                                                                 \
+    {cat_fwd_launch_m##m, cat_fwd_occupancy_m##m, cat_bwd_launch_m##m, cat_bwd_occupancy_m##m,     \
+     cat_fwd_multi_launch_m##m, cat_fwd_multi_occupancy_m##m}
 static const CLaunch kCat[TPCF_MAX_M + 1] = {
     TPCF_CROW(0),  TPCF_CROW(1),  TPCF_CROW(2),  TPCF_CROW(3),  TPCF_CROW(4),  TPCF_CROW(5),
     TPCF_CROW(6),  TPCF_CROW(7),  TPCF_CROW(8),  TPCF_CROW(9),  TPCF_CROW(10), TPCF_CROW(11),
@@ -378,6 +385,55 @@ tpcf_status catalog_backward(tpcf_plan_s* P, const float* d_delta, const float* 
     c.H = P->H;
     c.grad = d_grad;
     TRY_CUDA(kCat[P->M].bwd(g, c, P->bwd_grid, s));
+    return TPCF_OK;
+}
+
+// Three fields on the catalogue's points (tpcf_forward_multi on catalogue plans).
+tpcf_status catalog_forward_multi(tpcf_plan_s* P, const float* const* d_delta, const float* const* d_w, int64_t lo,
+                                  int64_t hi, double* d_zeta, double* d_norm, double* d_sums, cudaStream_t s) {
+    const CatDev& g = P->cat;
+    const int K = P->K, M = P->M;
+    const int nent = n_entries_multi(K, M);
+    if (!P->wdw_b) {  // the second and third fields' packed values and the slots, on the first call
+        const int occ = kCat[M].multi_occ(K);
+        if (occ < 1) {
+            char msg[160];
+            snprintf(msg, sizeof(msg),
+                     "tpcf_forward_multi: three fields' moments (K=%d, m_max=%d) do not fit in shared memory", K, M);
+            set_error(msg);
+            return TPCF_ERR_UNSUPPORTED;
+        }
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)P->num_sms * occ));
+        float2 *b, *c;
+        double *sl, *su;
+        TRY_CUDA(P->alloc(&b, g.n));
+        TRY_CUDA(P->alloc(&c, g.n));
+        TRY_CUDA(P->alloc(&sl, (size_t)grid * nent));
+        TRY_CUDA(P->alloc(&su, (size_t)nent));
+        P->wdw_c = c;
+        P->mslots = sl;
+        P->msums = su;
+        P->multi_grid = grid;
+        P->wdw_b = b;
+    }
+    float2* dst[3] = {P->wdw, P->wdw_b, P->wdw_c};
+    for (int f = 0; f < 3; ++f)
+        cat_pack_kernel<<<P->num_sms * 8, 256, 0, s>>>(g.n, g.orig, d_delta[f], d_w[f], dst[f]);
+    TRY_CUDA(cudaMemsetAsync(P->mslots, 0, sizeof(double) * (size_t)P->multi_grid * nent, s));
+    TRY_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(int), s));
+    MapCall c{};
+    c.wdw = P->wdw;
+    c.piv_lo = lo;
+    c.piv_hi = hi;
+    c.slots = P->mslots;
+    c.counter = P->counter;
+    c.status = P->status;
+    TRY_CUDA(kCat[M].multi(g, c, P->wdw_b, P->wdw_c, P->multi_grid, s));
+    reduce_slots_kernel<<<(nent + 127) / 128, 128, 0, s>>>(P->mslots, P->multi_grid, nent, P->msums);
+    const int nout = (M + 1) * K * K;
+    finalize_full_kernel<<<(nout + 127) / 128, 128, 0, s>>>(P->msums, K, M, d_zeta, d_norm, d_sums);
+    P->launches += 6;  // three packs, the pair kernel, reduce, finalize
+    TRY_CUDA(cudaGetLastError());
     return TPCF_OK;
 }
 

@@ -41,6 +41,8 @@ static int occupancy(Kern* k, size_t smem) {
 cudaError_t TPCF_CAT(map_fwd_launch_m, TPCF_M)(const MapDev& g, const MapCall& c, int grid, int variant,
                                                cudaStream_t s) {
     const size_t smem = tile_floats<TPCF_M>(g.K) * sizeof(float);
+    if (c.group > 1)  // shared neighbour lists (self pairs kept)
+        return launch(map_fwd_kernel<TPCF_M, false, false, 3, true>, smem, grid, g, c, s);
     if (c.self_subtract)
         return variant == 2 ? launch(map_fwd_kernel<TPCF_M, true, false, 2>, smem, grid, g, c, s)
                             : launch(map_fwd_kernel<TPCF_M, true, false, 3>, smem, grid, g, c, s);
@@ -143,6 +145,21 @@ cudaError_t TPCF_CAT(map_fwd_multi_launch_m, TPCF_M)(const MapDev& g, const MapC
 
 int TPCF_CAT(map_fwd_multi_occupancy_m, TPCF_M)(int K) {
     return occupancy(map_fwd_multi_kernel<TPCF_M>, multi_tile_floats(K, TPCF_M) * sizeof(float));
+}
+
+// Multi-field forward on a catalogue.
+cudaError_t TPCF_CAT(cat_fwd_multi_launch_m, TPCF_M)(const CatDev& g, const MapCall& c, const float2* wdwB,
+                                                     const float2* wdwC, int grid, cudaStream_t s) {
+    const size_t smem = cat_multi_bytes<TPCF_M>(g.K);
+    auto* k = cat_fwd_multi_kernel<TPCF_M>;
+    cudaError_t e = prefer_shared(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTHREADS, smem, s>>>(g, c, wdwB, wdwC);
+    return cudaGetLastError();
+}
+
+int TPCF_CAT(cat_fwd_multi_occupancy_m, TPCF_M)(int K) {
+    return occupancy(cat_fwd_multi_kernel<TPCF_M>, cat_multi_bytes<TPCF_M>(K));
 }
 
 // Forward that reads the caller's delta and w directly (no packed copy).

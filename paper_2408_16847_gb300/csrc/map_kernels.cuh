@@ -1252,7 +1252,7 @@ __device__ void tile_contract_tc(int K, float* base, double* slot, TcState& tc, 
 
 // One forward tile: the moments of its 32 pivots, then their partial sums added to
 // the CTA's slot.  Called by every thread of the CTA (contains barriers).
-template <int M, bool SELF, bool DIRECT>
+template <int M, bool SELF, bool DIRECT, bool GROUPED = false>
 __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int tile, double* slot, float* smem,
                                          int mr = M) {
     const int K = g.K;
@@ -1263,7 +1263,7 @@ __device__ __forceinline__ void fwd_tile(const MapDev& g, const MapCall& c, int 
     float* sPiv = sQW + K * TILE;
     const int lane = threadIdx.x & 31;
     const size_t nfl = tile_floats_rt(K, mr) - 2 * TILE;
-    const bool grouped = c.group > 1;
+    constexpr bool grouped = GROUPED;  // shared neighbour lists (c.group > 1): own instantiation
     const int2 tq = grouped ? c.gtiles[tile] : g.tiles[tile];
     if (tq.x < 0 || tq.x >= g.nrings) {
         if (threadIdx.x == 0) atomicOr(c.status, ST_BAD_TILE);
@@ -1362,7 +1362,7 @@ __device__ __forceinline__ void fwd_tile_tc(const MapDev& g, const MapCall& c, i
 
 // OCC: CTAs per SM the register allocation is sized for (3: 80 registers, 2: 128);
 // the autotuner picks the variant and the grid.
-template <int M, bool SELF, bool DIRECT, int OCC = 3>
+template <int M, bool SELF, bool DIRECT, int OCC = 3, bool GROUPED = false>
 __global__ void __launch_bounds__(NTHREADS, OCC) map_fwd_kernel(MapDev g, MapCall c) {
     extern __shared__ float smem[];
     __shared__ int s_tile;
@@ -1372,7 +1372,7 @@ __global__ void __launch_bounds__(NTHREADS, OCC) map_fwd_kernel(MapDev g, MapCal
         __syncthreads();
         const long long tile = c.tile_lo + s_tile;
         if (tile >= c.tile_hi) break;
-        fwd_tile<M, SELF, DIRECT>(g, c, (int)tile, slot, smem);
+        fwd_tile<M, SELF, DIRECT, GROUPED>(g, c, (int)tile, slot, smem);
     }
 }
 

@@ -45,7 +45,7 @@ struct tpcf_plan_s {
     // rings summed in registers per shared-memory flush
     // and, for the forward, the tile layout (1: quarter-turn runs, 0: consecutive pivots)
     struct Tune {
-        int variant = 3, ctas = 0, flush = 8, quad = 1;
+        int variant = 3, ctas = 0, flush = 8, quad = 0;
     } tune_fwd, tune_bwd;
     bool tuned = false;
     // per-call scratch

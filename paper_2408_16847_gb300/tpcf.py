@@ -207,7 +207,7 @@ class Plan:
 
     def set_launch_config(self, cfg: dict) -> None:
         f, b = cfg["forward"], cfg["adjoint"]
-        c = (ctypes.c_int32 * 7)(f["variant"], f["ctas_per_sm"], f["flush_rings"], f.get("quarter_turn_tiles", 1),
+        c = (ctypes.c_int32 * 7)(f["variant"], f["ctas_per_sm"], f["flush_rings"], f.get("quarter_turn_tiles", 0),
                                  b["variant"], b["ctas_per_sm"], b["flush_rings"])
         check(lib().tpcf_plan_set_launch_config(self._h, c), "tpcf_plan_set_launch_config")
 

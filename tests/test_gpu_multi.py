@@ -1,4 +1,4 @@
-"""The multi-field forward (tpcf_forward_multi, three fields on one map's pixels,
+"""The multi-field forward (tpcf_forward_multi, three fields on one plan's points,
 cyclic sum over the pivot field) against the oracle's zeta_multi, per multipole;
 one field reduces to the single-field forward; unsupported plans are rejected."""
 import numpy as np
@@ -83,3 +83,33 @@ def test_multi_rejects_unsupported_plans(cuda_device):
             p.forward_multi([(one, one)] * 3)
         assert e.value.status == 5
         p.close()
+
+
+@pytest.mark.parametrize("n,edges,M,pivots", [
+    (4000, [0.9, 2.1, 4.3, 7.7], 6, None),
+    (12000, list(np.geomspace(0.4, 6.0, 7)), 10, (2500, 7100)),
+])
+def test_catalogue_multi_field_vs_oracle(cuda_device, n, edges, M, pivots):
+    tpcf = _tpcf()
+    xyz = synth.clustered_catalog(n, 150, 0.8, synth.BASE_SEED + 1360 + n)
+    g = synth.rng(1361 + n)
+    fields = [((g.standard_normal(n) + 0.3 * f).astype(np.float32), g.uniform(0.5, 1.5, n).astype(np.float32))
+              for f in range(3)]
+    plan = tpcf.Plan.catalog(torch.from_numpy(np.ascontiguousarray(xyz)).to("cuda:0"), np.asarray(edges), M)
+    zeta, norm, sums = plan.forward_multi([(to_dev(d), to_dev(w)) for d, w in fields], pivots, want_sums=True)
+    plan.sync()
+    piv = None if pivots is None else np.arange(pivots[0], pivots[1])
+    ref = oracle.zeta_multi(xyz, [(d.astype(np.float64), w.astype(np.float64)) for d, w in fields],
+                            np.asarray(edges), M, pivots=piv)
+    assert ref["min_margin"] > 1e-12
+    assert rel_err_per_m(tpcf.as_complex(zeta).cpu().numpy(), ref["zeta"]).max() < TOL
+    assert rel_err_per_m(tpcf.as_complex(sums).cpu().numpy(), ref["S"]).max() < TOL
+    np.testing.assert_allclose(norm.cpu().numpy(), ref["D"], rtol=1e-6, atol=1e-6 * np.abs(ref["D"]).max())
+    # one field three times is the single-field catalogue forward
+    d, w = fields[0]
+    zm, nm = plan.forward_multi([(to_dev(d), to_dev(w))] * 3, pivots)
+    z1, n1 = plan.forward(to_dev(d), to_dev(w), pivots)
+    torch.cuda.synchronize()
+    assert rel_err_per_m(tpcf.as_complex(zm).cpu().numpy(), tpcf.as_complex(z1).cpu().numpy()).max() < 1e-6
+    np.testing.assert_allclose(nm.cpu().numpy(), 3 * n1.cpu().numpy(), rtol=1e-6)
+    plan.close()
