@@ -405,8 +405,10 @@ def setup_map(args, dev, rank):
         zo = s["zeta"]
         per_m = [float(np.abs(zg[m] - zo[m]).max() / max(np.abs(zo[m]).max(), 1e-300)) for m in range(M + 1)]
         glob = float(np.abs(zg - zo).max() / np.abs(zo).max())
+        scale = [float(np.abs(zo[m]).max() / np.abs(zo).max()) for m in range(M + 1)]
         return s, {"pivots": s["hi"] - s["lo"], "max_rel_err_per_m": max(per_m),
-                   "rel_err_per_m": per_m, "max_rel_err_vs_max_zeta": glob, "tolerance_per_m": 1e-5}
+                   "rel_err_per_m": per_m, "max_rel_err_vs_max_zeta": glob, "tolerance_per_m": 1e-5,
+                   "max_abs_zeta_m_over_max_abs_zeta": scale}
 
     def roof_fwd(ms, clk, sms):
         # ms: the forward step (pack + pair kernel + two reductions; the pair kernel is
