@@ -459,6 +459,21 @@ def setup_map(args, dev, rank):
         if args.fb_steps > 0:
             W["part_fb"] = dict(name="forward_adjoint", step=step_fb, warm=warm_adjoint, steps=args.fb_steps,
                                 roofline=lambda t1, t2, clk, sms: roof_fb(t1 + t2, t1, clk, sms))
+        if args.grouped > 1:
+            # shared neighbour lists (tpcf_forward_grouped): time and deviation from the
+            # exact forward of the timed region
+            def step_grouped(ev=None):
+                state["zg"], _ = plan.forward_grouped(d_dev, w_dev, args.grouped, piv)
+                if ev is not None:
+                    ev.record(torch.cuda.current_stream())
+
+            def deviation():
+                zg = tpcf.as_complex(state["zg"]).cpu().numpy()
+                ze = tpcf.as_complex(state["zeta"]).cpu().numpy()
+                return [float(np.abs(zg[m] - ze[m]).max() / max(np.abs(ze[m]).max(), 1e-300)) for m in range(M + 1)]
+
+            W["part_grouped"] = dict(group=args.grouped, step=step_grouped, steps=max(2, args.fb_steps),
+                                     deviation=deviation)
     return W
 
 
@@ -801,6 +816,16 @@ def run_gpu(args):
                 "roofline": roof_p, "clocks": p_clk}
         log("[rank %d] forward + adjoint: %.1f ms/step" % (rank, p_tot / P["steps"]))
 
+    gpart = None
+    if W.get("part_grouped") is not None:
+        G = W["part_grouped"]
+        G["step"]()  # builds the run tile list and warms the kernel
+        g_tot, _, _, g_clk = timed(G["step"], G["steps"])
+        gpart = {"group": G["group"], "steps": G["steps"], "ms": g_tot / G["steps"],
+                 "speedup_vs_forward": (ms1 / args.steps) / (g_tot / G["steps"]),
+                 "deviation_from_exact_per_m": G["deviation"](), "clocks": g_clk}
+        log("[rank %d] shared lists (group %d): %.1f ms/step" % (rank, G["group"], g_tot / G["steps"]))
+
     result = None
     if rank == 0:
         roof = W["roofline"](ms1 / args.steps, ms2 / args.steps, clk, sms)
@@ -822,6 +847,8 @@ def run_gpu(args):
             parts[b] = {"ms": ms2 / args.steps}
         if part is not None:
             parts["forward_adjoint"] = part
+        if gpart is not None:
+            parts["forward_grouped"] = gpart
         result = {
             "metric": METRIC,
             "value": value,
@@ -912,6 +939,9 @@ def main():
     ap.add_argument("--pass", dest="pass_", default="auto", choices=["auto", "both", "forward"],
                     help="map workloads: the timed step is the forward (full-sky maps) or the forward + "
                          "adjoint (the masked map) by default")
+    ap.add_argument("--grouped", type=int, default=0,
+                    help="also time the shared-neighbour-list forward with runs of this many ring pixels "
+                         "(map workloads, one GPU) and report its deviation from the exact forward")
     ap.add_argument("--fb-steps", type=int, default=2,
                     help="map workloads timed on the forward: full forward + adjoint steps reported in parts")
     ap.add_argument("--e2e-steps", type=int, default=1,
