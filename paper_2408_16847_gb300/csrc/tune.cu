@@ -207,8 +207,8 @@ extern "C" tpcf_status tpcf_plan_autotune(tpcf_plan plan, const float* d_delta, 
         for (int variant = 3; variant >= 2 && st == TPCF_OK; --variant) {
             const int occ = bwd ? map_bwd_occupancy(M, K, variant) : map_fwd_occupancy(M, K, self, variant);
             for (int ctas = occ; ctas >= std::max(1, occ - 1) && st == TPCF_OK; --ctas) {
-                const int flushes[3] = {4, 8, 16};
-                for (int fi = 0; fi < 3 && st == TPCF_OK; ++fi) {
+                const int flushes[4] = {4, 8, 16, 32};
+                for (int fi = 0; fi < 4 && st == TPCF_OK; ++fi) {
                     T.variant = variant;
                     T.ctas = ctas;
                     T.flush = flushes[fi];
